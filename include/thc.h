@@ -1,0 +1,197 @@
+/*
+ * thc.h -- C ABI of the GB300 (sm_103a) THC-MPO Krylov library.
+ *
+ * The library applies a tensor-hypercontraction (THC) factorised molecular
+ * Hamiltonian to a matrix-product state (MPS) and recompresses the result,
+ * the hot path of the THC-MPO Krylov method of arXiv 2409.12708.  Every
+ * numerical step runs in this library's own CUDA kernels on one GPU.
+ *
+ * Conventions shared by all calls
+ * -------------------------------
+ *  - Pointers called "device" point to GPU memory of the current device;
+ *    "host" pointers point to CPU memory.  Inputs are never modified.
+ *  - All work is enqueued on `stream` (a cudaStream_t, NULL = legacy default
+ *    stream).  Calls that return scalars to the host (mps_inner, the Krylov
+ *    drivers) synchronise `stream` before returning; the others return as soon
+ *    as the work is enqueued, and their outputs are valid once `stream` reaches
+ *    that point.
+ *  - Errors: a call returns a thc_status.  THC_EINVAL means a shape, size or
+ *    argument was rejected before any work was enqueued and no output was
+ *    written.  Other non-OK statuses may leave outputs partially written.
+ *    thc_last_error() returns a message for the last non-OK status of the
+ *    calling thread.
+ *  - Memory: outputs (thc_mps with owner != NULL) and internal workspace are
+ *    obtained from the caller's thc_allocator (stream-ordered alloc/free
+ *    callbacks); a NULL allocator means cudaMallocAsync/cudaFreeAsync on
+ *    `stream`.  Workspace is released before the call returns (stream-ordered).
+ *
+ * MPS layout (Sec. 2.1, the MPS equation): L order-3 site tensors, site i has
+ * shape [bond[i], d, bond[i+1]] stored row-major (right bond fastest), with
+ * bond[0] = bond[L] = 1 and d = 4.  The local basis index is 2*n_up + n_dn
+ * (App. C: b_up = c (x) I2, b_dn = Z (x) c, spin-up major).
+ */
+#ifndef THC_H
+#define THC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define THC_MAX_SITES 64
+
+typedef enum {
+    THC_OK = 0,
+    THC_EINVAL = 1,        /* bad argument / shape / dtype; nothing written          */
+    THC_ENOMEM = 2,        /* allocator returned NULL                                 */
+    THC_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed             */
+    THC_ENONFINITE = 4,    /* a NaN/Inf was detected in an input or a result          */
+    THC_ETIMEOUT = 5,      /* an iteration budget ran out (e.g. Jacobi sweeps)        */
+    THC_EBREAKDOWN = 6,    /* Krylov breakdown: the Krylov space is exhausted         */
+    THC_EUNSUPPORTED = 7   /* valid request this build does not implement             */
+} thc_status;
+
+/* Storage dtype of MPS site tensors. */
+typedef enum { THC_F64 = 0, THC_F32 = 1, THC_C64 = 2, THC_C128 = 3 } thc_dtype;
+
+/* Compute path.  FP64: every step in float64 ("plain FP64 path").  FP32: site
+ * tensors, contractions, QR and Jacobi SVD in float32; singular values are
+ * accumulated and the truncation decided in float64; inner products and the
+ * Krylov projected problems are float64. */
+typedef enum { THC_PATH_FP64 = 0, THC_PATH_FP32 = 1 } thc_path;
+
+/* Stream-ordered allocator supplied by the caller (e.g. PyTorch's caching
+ * allocator).  alloc returns NULL on failure. */
+typedef struct {
+    void* (*alloc)(size_t bytes, void* stream, void* ctx);
+    void  (*free)(void* ptr, void* stream, void* ctx);
+    void* ctx;
+} thc_allocator;
+
+/* MPS descriptor.  For inputs the caller fills L, d, dtype, bond[0..L] and
+ * site[0..L-1] (device pointers) and sets owner = NULL; the library reads the
+ * site tensors only.  For outputs the library fills every field; all sites live
+ * in one device block `owner` obtained from the allocator, released by
+ * thc_mps_free. */
+typedef struct {
+    int L;
+    int d;
+    thc_dtype dtype;
+    int bond[THC_MAX_SITES + 1];
+    void* site[THC_MAX_SITES];
+    void* owner;
+} thc_mps;
+
+/* THC-factorised Hamiltonian, Eq. 1 with Eq. thc: device float64 arrays,
+ * row-major: t[L*L] (symmetric one-body integrals t_pq), chi[L*N]
+ * (chi[p*N + mu] = chi^mu_p), zeta[N*N] (symmetric zeta^{mu nu}). */
+typedef struct {
+    int L;
+    int N;
+    const double* t;
+    const double* chi;
+    const double* zeta;
+} thc_hamiltonian;
+
+/* Options.  D_max: MPS bond cap after every compression (the paper's M).
+ * tol: relative discarded-weight tolerance of the truncation (0 = cap only).
+ * term_begin/term_end: half-open range of term indices to apply (-1 = all);
+ * Coulomb terms G_{mu s, nu s'} have index ((s'*N + nu)*2 + s)*N + mu and
+ * kinetic terms T_{i s} index 4N^2 + s*L + i.  batch: terms in flight
+ * (0 = choose from free memory). */
+typedef struct {
+    int D_max;
+    double tol;
+    thc_path path;
+    long term_begin;
+    long term_end;
+    int batch;
+} thc_opts;
+
+/* H|psi> as a compressed MPS: Alg. 1 of the paper (the reuse of
+ * G_{nu s'}|psi> across all (mu, s)), plus the kinetic terms of App. D; each of
+ * the bond-2 ladder MPOs of the elementary-MPO equations is applied and
+ * followed by the QR-then-SVD compression of Fig. 3, and the compressed terms
+ * are summed by the pairwise reduction of Sec. 4.5.  psi must have dtype
+ * F64 (path FP64) or F32 (path FP32).  `out` receives a library-owned MPS of
+ * the same dtype whose bonds are at most D_max. */
+thc_status thc_apply_H(const thc_hamiltonian* H, const thc_mps* psi, const thc_opts* opts,
+                       thc_mps* out, const thc_allocator* alloc, void* stream);
+
+/* One elementary MPO (a ladder operator sum_s coef_s a_{s,sigma}, or its
+ * creation counterpart when dagger != 0) applied to psi and compressed
+ * (Sec. 3.1, Fig. 3).  coef: device float64 [L]; sigma: 0 = up, 1 = down. */
+thc_status thc_layer_apply(const thc_mps* psi, const double* coef, int sigma, int dagger,
+                           const thc_opts* opts, thc_mps* out,
+                           const thc_allocator* alloc, void* stream);
+
+/* Compression of Fig. 3 alone: QR sweep to right-canonical form, then the
+ * left-to-right SVD truncation sweep (no renormalisation). */
+thc_status thc_compress(const thc_mps* psi, const thc_opts* opts, thc_mps* out,
+                        const thc_allocator* alloc, void* stream);
+
+/* <phi|psi> = sum conj(phi) psi by transfer matrices, accumulated in float64.
+ * out_re / out_im: host pointers (out_im may be NULL for real states). */
+thc_status mps_inner(const thc_mps* phi, const thc_mps* psi, double* out_re, double* out_im,
+                     void* stream);
+
+/* compress(sum_i coeff_i |x_i>): direct sums and compressions of the pairwise
+ * reduction (Sec. 3.2, Sec. 4.5).  coeff_re/coeff_im: host float64 [n]
+ * (coeff_im may be NULL).  All xs share L and dtype. */
+thc_status mps_add_compress(int n, const double* coeff_re, const double* coeff_im,
+                            const thc_mps* const* xs, const thc_opts* opts, thc_mps* out,
+                            const thc_allocator* alloc, void* stream);
+
+/* Lanczos ground state (Sec. 2.2): K Krylov vectors by Gram-Schmidt, the full
+ * projected matrix Htil_jk = <v_j|H v_k> and overlap S_jk, the correction of
+ * Eq. reortho / Eq. eff_H by canonical orthogonalisation, float64 eigensolver.
+ * energy: host double; ritz: host double[K] (ascending Ritz values, unused
+ * entries NaN; may be NULL); ground: optional output MPS of the Ritz vector
+ * (NULL to skip).  Returns THC_EBREAKDOWN only if not even one vector exists. */
+thc_status krylov_lanczos_ground(const thc_hamiltonian* H, const thc_mps* psi0, int K,
+                                 const thc_opts* opts, double* energy, double* ritz,
+                                 thc_mps* ground, const thc_allocator* alloc, void* stream);
+
+/* One global-Krylov time step (Sec. 2.2, Eq. Krylov_combination):
+ * a(dt) = exp(-i dt Heff) a(0), psi(dt) = compress(sum_i a_i v_i) renormalised
+ * to the norm of psi; lost_norm (host, may be NULL) = 1 - ||psi(dt)||/||psi||
+ * before renormalisation.  `out` is complex (C128 for path FP64, C64 for FP32). */
+thc_status krylov_expm_apply(const thc_hamiltonian* H, const thc_mps* psi, double dt, int K,
+                             const thc_opts* opts, thc_mps* out, double* lost_norm,
+                             const thc_allocator* alloc, void* stream);
+
+/* Eigen-decomposition t = U diag(lambda) U^T of the one-body integrals (App. D,
+ * Eq. t_diagonalization) by a float64 Jacobi kernel: t device [L*L] row-major,
+ * lambda device [L] ascending, u device [L*L] row-major with column i the
+ * eigenvector of lambda_i. */
+thc_status thc_kinetic_factors(int L, const double* t, double* lambda, double* u, void* stream);
+
+/* Release a library-owned MPS (owner != NULL) and clear the descriptor. */
+void thc_mps_free(thc_mps* m, const thc_allocator* alloc, void* stream);
+
+/* Message for the last non-OK status returned on the calling thread. */
+const char* thc_last_error(void);
+
+/* Build description (arch, compiler) as a static string. */
+const char* thc_build_info(void);
+
+/* Diagnostics (no counterpart in the paper).  thc_kernel_launches: number of
+ * CUDA kernels this library has launched in the process so far.
+ * thc_profile_enable(1) makes every later launch record a pair of CUDA events
+ * on its own stream; thc_profile_read synchronises those events, writes a JSON
+ * object {"name": {"launches": n, "ms": total}, ...} of the per-kernel sums
+ * since the last read into buf (NUL-terminated, truncated to len), resets the
+ * sums, and returns the number of bytes the full text needs.  The entry
+ * "jacobi_budget_exhausted" counts Jacobi SVDs that used their whole sweep
+ * budget ("ms" then holds the largest remaining row cosine).  Profiling adds
+ * host work per launch; leave it off for timed runs. */
+unsigned long long thc_kernel_launches(void);
+void thc_profile_enable(int on);
+int thc_profile_read(char* buf, int len);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* THC_H */

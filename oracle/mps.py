@@ -9,6 +9,7 @@ with MPO bonds a, b and physical output/input indices m, n (Eq. MPO_def).
 from __future__ import annotations
 
 import numpy as np
+import scipy.linalg as sla
 
 # --- App. C: local operators on one spatial orbital (index 2*n_up + n_dn) -----
 C2 = np.array([[0.0, 1.0], [0.0, 0.0]])
@@ -96,6 +97,15 @@ def mpo_to_dense(W) -> np.ndarray:
     return O[:, :, 0]
 
 
+def svd(M):
+    """Thin SVD; LAPACK's divide-and-conquer driver with the QR-iteration driver
+    as fallback when the former reports non-convergence."""
+    try:
+        return np.linalg.svd(M, full_matrices=False)
+    except np.linalg.LinAlgError:
+        return sla.svd(M, full_matrices=False, lapack_driver="gesvd")
+
+
 def keep_count(s: np.ndarray, D_max: int, tol: float) -> int:
     """Truncation rule (reading of Sec. 2.2 / Fig. 3): s sorted descending.
 
@@ -134,7 +144,7 @@ def compress(A, D_max: int, tol: float = 0.0, return_discarded: bool = False):
     discarded = []
     for i in range(L - 1):
         Dl, d, Dr = A[i].shape
-        u, s, vh = np.linalg.svd(A[i].reshape(Dl * d, Dr), full_matrices=False)
+        u, s, vh = svd(A[i].reshape(Dl * d, Dr))
         k = keep_count(s, D_max, tol)
         discarded.append(float(np.sum(s[k:] ** 2)))
         A[i] = u[:, :k].reshape(Dl, d, k)

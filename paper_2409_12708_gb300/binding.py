@@ -1,0 +1,290 @@
+"""Python binding of the C ABI in include/thc.h (ctypes; argument marshalling only).
+
+Every numerical step runs inside libthc.so's CUDA kernels.  PyTorch supplies
+device memory (its caching allocator is handed to the library as the
+thc_allocator callbacks), the current CUDA stream, and the tensors that hold
+site tensors.  There is no CPU fallback: if the library is missing, importing
+this module raises.
+
+An MPS is a list of L CUDA tensors, site i of shape [chi_i, 4, chi_{i+1}]
+(float64 for path "fp64", float32 for path "fp32").
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libthc.so")
+
+MAX_SITES = 64
+OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, EBREAKDOWN, EUNSUPPORTED = range(8)
+F64, F32, C64, C128 = range(4)
+PATH_FP64, PATH_FP32 = 0, 1
+_PATHS = {"fp64": PATH_FP64, "fp32": PATH_FP32}
+_DT = {PATH_FP64: (F64, torch.float64), PATH_FP32: (F32, torch.float32)}
+_TORCH_OF = {F64: torch.float64, F32: torch.float32}
+
+
+class ThcError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"thc status {status}: {msg}")
+        self.status = status
+
+
+class thc_mps(C.Structure):
+    _fields_ = [("L", C.c_int), ("d", C.c_int), ("dtype", C.c_int),
+                ("bond", C.c_int * (MAX_SITES + 1)), ("site", C.c_void_p * MAX_SITES),
+                ("owner", C.c_void_p)]
+
+
+class thc_hamiltonian(C.Structure):
+    _fields_ = [("L", C.c_int), ("N", C.c_int), ("t", C.c_void_p), ("chi", C.c_void_p),
+                ("zeta", C.c_void_p)]
+
+
+class thc_opts(C.Structure):
+    _fields_ = [("D_max", C.c_int), ("tol", C.c_double), ("path", C.c_int),
+                ("term_begin", C.c_long), ("term_end", C.c_long), ("batch", C.c_int)]
+
+
+_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+
+class thc_allocator(C.Structure):
+    _fields_ = [("alloc", _ALLOC_FN), ("free", _FREE_FN), ("ctx", C.c_void_p)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run __graft_entry__.build() first")
+    lib = C.CDLL(LIB_PATH)
+    P = C.POINTER
+    sig = {
+        "thc_apply_H": [P(thc_hamiltonian), P(thc_mps), P(thc_opts), P(thc_mps), P(thc_allocator), C.c_void_p],
+        "thc_layer_apply": [P(thc_mps), C.c_void_p, C.c_int, C.c_int, P(thc_opts), P(thc_mps),
+                            P(thc_allocator), C.c_void_p],
+        "thc_compress": [P(thc_mps), P(thc_opts), P(thc_mps), P(thc_allocator), C.c_void_p],
+        "mps_inner": [P(thc_mps), P(thc_mps), P(C.c_double), P(C.c_double), C.c_void_p],
+        "mps_add_compress": [C.c_int, P(C.c_double), P(C.c_double), P(P(thc_mps)), P(thc_opts),
+                             P(thc_mps), P(thc_allocator), C.c_void_p],
+        "krylov_lanczos_ground": [P(thc_hamiltonian), P(thc_mps), C.c_int, P(thc_opts), P(C.c_double),
+                                  P(C.c_double), P(thc_mps), P(thc_allocator), C.c_void_p],
+        "krylov_expm_apply": [P(thc_hamiltonian), P(thc_mps), C.c_double, C.c_int, P(thc_opts),
+                              P(thc_mps), P(C.c_double), P(thc_allocator), C.c_void_p],
+        "thc_kinetic_factors": [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    lib.thc_mps_free.argtypes = [P(thc_mps), P(thc_allocator), C.c_void_p]
+    lib.thc_mps_free.restype = None
+    lib.thc_last_error.restype = C.c_char_p
+    lib.thc_build_info.restype = C.c_char_p
+    lib.thc_kernel_launches.restype = C.c_ulonglong
+    lib.thc_profile_enable.argtypes = [C.c_int]
+    lib.thc_profile_enable.restype = None
+    lib.thc_profile_read.argtypes = [C.c_char_p, C.c_int]
+    lib.thc_profile_read.restype = C.c_int
+    return lib
+
+
+LIB = _load()
+
+# the declared entry points of include/thc.h (checked by the CPU tests)
+EXPORTED = ("thc_apply_H", "thc_layer_apply", "thc_compress", "mps_inner", "mps_add_compress",
+            "krylov_lanczos_ground", "krylov_expm_apply", "thc_kinetic_factors", "thc_mps_free",
+            "thc_last_error", "thc_build_info", "thc_kernel_launches", "thc_profile_enable",
+            "thc_profile_read")
+
+
+# --------------------------------------------------------------------- allocator
+def _torch_alloc(size, stream, ctx):
+    try:
+        return torch.cuda.caching_allocator_alloc(int(size), stream=int(stream or 0))
+    except Exception:  # out of memory: the library turns NULL into THC_ENOMEM
+        return None
+
+
+def _torch_free(ptr, stream, ctx):
+    if ptr:
+        torch.cuda.caching_allocator_delete(ptr)
+
+
+_ALLOC_CB = _ALLOC_FN(_torch_alloc)
+_FREE_CB = _FREE_FN(_torch_free)
+TORCH_ALLOCATOR = thc_allocator(_ALLOC_CB, _FREE_CB, None)
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _check(status):
+    if status != OK:
+        raise ThcError(status, LIB.thc_last_error().decode())
+
+
+# --------------------------------------------------------------------- marshalling
+_CODE_OF = {torch.float64: F64, torch.float32: F32}
+
+
+def _desc(sites, dtype_code=None):
+    # the dtype code always describes the tensors; the library checks it
+    # against the requested compute path
+    m = thc_mps()
+    m.L = len(sites)
+    m.d = 4
+    m.dtype = _CODE_OF.get(sites[0].dtype, -1)
+    m.bond[0] = sites[0].shape[0]
+    for i, s in enumerate(sites):
+        if not (s.is_cuda and s.is_contiguous() and s.dim() == 3 and s.shape[1] == 4):
+            raise ValueError("site tensors must be contiguous CUDA tensors [chi_l, 4, chi_r]")
+        m.bond[i + 1] = s.shape[2]
+        m.site[i] = s.data_ptr()
+    m.owner = None
+    return m
+
+
+class _View:
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (ptr, False), "version": 3, "strides": None}
+
+
+def _take(m):
+    """Copy a library-owned output MPS into torch tensors and release the block."""
+    tdt = _TORCH_OF[m.dtype]
+    typestr = "<f8" if tdt == torch.float64 else "<f4"
+    out = []
+    for i in range(m.L):
+        shape = (m.bond[i], 4, m.bond[i + 1])
+        out.append(torch.as_tensor(_View(m.site[i], shape, typestr), device="cuda").clone())
+    LIB.thc_mps_free(C.byref(m), C.byref(TORCH_ALLOCATOR), _stream())
+    return out
+
+
+def _ham(t, chi, zeta):
+    for x in (t, chi, zeta):
+        if not (x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()):
+            raise ValueError("t, chi, zeta must be contiguous float64 CUDA tensors")
+    h = thc_hamiltonian()
+    h.L, h.N = chi.shape
+    h.t, h.chi, h.zeta = t.data_ptr(), chi.data_ptr(), zeta.data_ptr()
+    return h
+
+
+def _opts(D_max, tol, path, term_begin=-1, term_end=-1, batch=0):
+    return thc_opts(int(D_max), float(tol), _PATHS[path], int(term_begin), int(term_end), int(batch))
+
+
+def _code(path):
+    return _DT[_PATHS[path]][0]
+
+
+# --------------------------------------------------------------------- entry points
+def thc_apply_H(t, chi, zeta, psi, D_max, tol=0.0, path="fp64", term_begin=-1, term_end=-1, batch=0):
+    h = _ham(t, chi, zeta)
+    d = _desc(psi, _code(path))
+    o = _opts(D_max, tol, path, term_begin, term_end, batch)
+    out = thc_mps()
+    _check(LIB.thc_apply_H(C.byref(h), C.byref(d), C.byref(o), C.byref(out), C.byref(TORCH_ALLOCATOR),
+                           _stream()))
+    return _take(out)
+
+
+def thc_layer_apply(psi, coef, sigma, dagger, D_max, tol=0.0, path="fp64"):
+    if not (coef.is_cuda and coef.dtype == torch.float64):
+        raise ValueError("coef must be a float64 CUDA tensor")
+    d = _desc(psi, _code(path))
+    o = _opts(D_max, tol, path)
+    out = thc_mps()
+    _check(LIB.thc_layer_apply(C.byref(d), coef.data_ptr(), int(sigma), int(dagger), C.byref(o),
+                               C.byref(out), C.byref(TORCH_ALLOCATOR), _stream()))
+    return _take(out)
+
+
+def thc_compress(psi, D_max, tol=0.0, path="fp64"):
+    d = _desc(psi, _code(path))
+    o = _opts(D_max, tol, path)
+    out = thc_mps()
+    _check(LIB.thc_compress(C.byref(d), C.byref(o), C.byref(out), C.byref(TORCH_ALLOCATOR), _stream()))
+    return _take(out)
+
+
+def mps_inner(phi, psi):
+    code = F64 if phi[0].dtype == torch.float64 else F32
+    a, b = _desc(phi, code), _desc(psi, code)
+    re, im = C.c_double(), C.c_double()
+    _check(LIB.mps_inner(C.byref(a), C.byref(b), C.byref(re), C.byref(im), _stream()))
+    return re.value
+
+
+def mps_add_compress(coeffs, xs, D_max, tol=0.0, path="fp64"):
+    n = len(xs)
+    descs = [_desc(x, _code(path)) for x in xs]
+    arr = (C.POINTER(thc_mps) * n)(*[C.pointer(d) for d in descs])
+    cre = (C.c_double * n)(*[float(c) for c in coeffs])
+    o = _opts(D_max, tol, path)
+    out = thc_mps()
+    _check(LIB.mps_add_compress(n, cre, None, arr, C.byref(o), C.byref(out), C.byref(TORCH_ALLOCATOR),
+                                _stream()))
+    return _take(out)
+
+
+def krylov_lanczos_ground(t, chi, zeta, psi0, K, D_max, tol=0.0, path="fp64", want_ground=False, batch=0):
+    h = _ham(t, chi, zeta)
+    d = _desc(psi0, _code(path))
+    o = _opts(D_max, tol, path, batch=batch)
+    e = C.c_double()
+    ritz = (C.c_double * K)()
+    g = thc_mps()
+    _check(LIB.krylov_lanczos_ground(C.byref(h), C.byref(d), int(K), C.byref(o), C.byref(e), ritz,
+                                     C.byref(g) if want_ground else None, C.byref(TORCH_ALLOCATOR),
+                                     _stream()))
+    ground = _take(g) if want_ground else None
+    return e.value, [ritz[i] for i in range(K)], ground
+
+
+def krylov_expm_apply(t, chi, zeta, psi, dt, K, D_max, tol=0.0, path="fp64"):
+    h = _ham(t, chi, zeta)
+    d = _desc(psi, _code(path))
+    o = _opts(D_max, tol, path)
+    out = thc_mps()
+    lost = C.c_double()
+    _check(LIB.krylov_expm_apply(C.byref(h), C.byref(d), float(dt), int(K), C.byref(o), C.byref(out),
+                                 C.byref(lost), C.byref(TORCH_ALLOCATOR), _stream()))
+    return _take(out), lost.value
+
+
+def thc_kinetic_factors(t):
+    L = t.shape[0]
+    lam = torch.empty(L, dtype=torch.float64, device=t.device)
+    u = torch.empty(L, L, dtype=torch.float64, device=t.device)
+    _check(LIB.thc_kinetic_factors(L, t.data_ptr(), lam.data_ptr(), u.data_ptr(), _stream()))
+    return lam, u
+
+
+def build_info():
+    return LIB.thc_build_info().decode()
+
+
+def kernel_launches():
+    return int(LIB.thc_kernel_launches())
+
+
+def profile_enable(on=True):
+    LIB.thc_profile_enable(1 if on else 0)
+
+
+def profile_read():
+    import json
+    buf = C.create_string_buffer(1 << 20)
+    n = LIB.thc_profile_read(buf, len(buf))
+    if n > len(buf):
+        raise RuntimeError("profile text truncated")
+    return json.loads(buf.value.decode())

@@ -1,0 +1,343 @@
+// engine_impl.cuh -- Engine<T>: the hot path of the THC-MPO method on one GPU.
+#pragma once
+
+#include "engine.cuh"
+
+namespace thc {
+
+__global__ void k_pair_src(int* a, int* b, int B, int start) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < B) {
+        a[i] = start + 2 * i;
+        b[i] = start + 2 * i + 1;
+    }
+}
+
+// Per-wave scratch for all plans of one call (sized by the largest plan).
+template <class T>
+struct Work {
+    int B = 0;
+    long sWide = 0, sL = 0, sC = 0, sZ = 0, sV = 0, sTw = 0, sSv = 0;
+    T *wide = nullptr, *Lb[2] = {nullptr, nullptr}, *C = nullptr, *W = nullptr, *Z = nullptr;
+    T *V = nullptr, *M[2] = {nullptr, nullptr}, *Tw = nullptr;
+    double* sv = nullptr;
+    int* keep = nullptr;
+    // per-term layer data
+    T *coef1 = nullptr, *coef2 = nullptr, *pcoef = nullptr;
+    int *op1 = nullptr, *op2 = nullptr, *src = nullptr, *srcA = nullptr, *srcB = nullptr;
+};
+
+template <class T>
+struct Engine {
+    cudaStream_t st;
+    Alloc al;
+    int* dflag = nullptr;  // device status word
+    double* ddbg = nullptr;  // device diagnostics of a non-converged Jacobi ([4])
+    int sms = 152;
+
+    Engine(cudaStream_t s, const thc_allocator* a) : st(s) {
+        al.a = a;
+        al.st = s;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        static bool attrs_done = false;
+        if (!attrs_done) {
+            set_attrs();
+            attrs_done = true;
+        }
+    }
+
+    // Opt in to large dynamic shared memory: the per-block limit minus the
+    // kernel's static shared memory.
+    template <class K>
+    static void opt_in(K kern, int want) {
+        cudaFuncAttributes fa;
+        THC_CUDA(cudaFuncGetAttributes(&fa, kern));
+        int dev = 0, optin = 0;
+        THC_CUDA(cudaGetDevice(&dev));
+        THC_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        const int v = std::min<int>(want, optin - (int)fa.sharedSizeBytes);
+        THC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
+    }
+    static void set_attrs() {
+        const int big = 1 << 30;
+        opt_in(k_qr<T>, big);
+        opt_in(k_jacobi_select<T, 4>, big);
+        opt_in(k_jacobi_select<T, 8>, big);
+        opt_in(k_jacobi_select<T, 16>, big);
+        opt_in(k_jacobi_select<T, 32>, big);
+        opt_in(k_svd_finalize<T>, big);
+        opt_in(k_kinetic_factors, (int)KINETIC_SMEM);
+        opt_in(k_krylov_small, (int)KRYLOV_SMEM);
+    }
+
+    void check() { THC_CUDA(cudaGetLastError()); }
+
+    // ---------------------------------------------------------------- work
+    void alloc_work(Scratch& sc, Work<T>& w, int B, const std::vector<const Plan*>& plans) {
+        Plan mx;
+        for (auto* p : plans) {
+            mx.wsize = std::max(mx.wsize, p->wsize);
+            mx.maxL = std::max(mx.maxL, p->maxL);
+            mx.maxC = std::max(mx.maxC, p->maxC);
+            mx.maxZ = std::max(mx.maxZ, p->maxZ);
+            mx.maxV = std::max(mx.maxV, p->maxV);
+            mx.maxTw = std::max(mx.maxTw, p->maxTw);
+            mx.maxKout = std::max(mx.maxKout, p->maxKout);
+        }
+        w.B = B;
+        w.sWide = std::max(1L, mx.wsize);
+        w.sL = std::max(1L, mx.maxL);
+        w.sC = std::max(1L, mx.maxC);
+        w.sZ = std::max(1L, mx.maxZ);
+        w.sV = std::max(1L, mx.maxV);
+        w.sTw = std::max(1L, mx.maxTw);
+        w.sSv = std::max(1L, mx.maxKout);
+        w.wide = sc.get<T>((size_t)B * w.sWide);
+        w.Lb[0] = sc.get<T>((size_t)B * w.sL);
+        w.Lb[1] = sc.get<T>((size_t)B * w.sL);
+        w.C = sc.get<T>((size_t)B * w.sC);
+        w.W = sc.get<T>((size_t)B * w.sC);
+        w.Z = sc.get<T>((size_t)B * w.sZ);
+        w.V = sc.get<T>((size_t)B * w.sV);
+        w.M[0] = sc.get<T>((size_t)B * w.sV);
+        w.M[1] = sc.get<T>((size_t)B * w.sV);
+        w.Tw = sc.get<T>((size_t)B * w.sTw);
+        w.sv = sc.get<double>((size_t)B * w.sSv);
+        w.keep = sc.get<int>((size_t)B);
+        const int L = plans.empty() ? 1 : plans[0]->L;
+        w.coef1 = sc.get<T>((size_t)B * L);
+        w.coef2 = sc.get<T>((size_t)B * L);
+        w.pcoef = sc.get<T>((size_t)2 * B);
+        w.op1 = sc.get<int>((size_t)B);
+        w.op2 = sc.get<int>((size_t)B);
+        w.src = sc.get<int>((size_t)B);
+        w.srcA = sc.get<int>((size_t)B);
+        w.srcB = sc.get<int>((size_t)B);
+    }
+
+    static size_t work_bytes_per_term(const std::vector<const Plan*>& plans) {
+        long wsize = 0, maxL = 0, maxC = 0, maxZ = 0, maxV = 0, maxTw = 0, kout = 0;
+        int L = 1;
+        for (auto* p : plans) {
+            wsize = std::max(wsize, p->wsize);
+            maxL = std::max(maxL, p->maxL);
+            maxC = std::max(maxC, p->maxC);
+            maxZ = std::max(maxZ, p->maxZ);
+            maxV = std::max(maxV, p->maxV);
+            maxTw = std::max(maxTw, p->maxTw);
+            kout = std::max(kout, p->maxKout);
+            L = p->L;
+        }
+        return sizeof(T) * (size_t)(wsize + 2 * maxL + 2 * maxC + maxZ + 3 * maxV + maxTw + 2 * L + 2) +
+               sizeof(double) * kout + 8 * sizeof(int);
+    }
+
+    // ------------------------------------------------------------ compress
+    // Expand (bond-2 MPO layer or direct sum) and compress a batch of B terms.
+    // ex: loader with the term-level fields set (mode, inputs, coefficients);
+    // the per-site fields are filled here.  Output: out + b*out_stride, profile P.out.
+    void compress(const Plan& P, int B, ExpandA<T> ex, T* out, long out_stride, Work<T>& w) {
+        const int L = P.L;
+        if (L < 2) throw Error(THC_EINVAL, "L >= 2 required");
+        Profile pA(P.inA), pO(P.out);
+        Profile pB = P.mode == MODE_DIRSUM ? Profile(P.inB) : Profile();
+        ex.L = L;
+        // ---- QR sweep, right to left: X_s = expand(site s) * L_{s+1}; X_s = L_s Q_s
+        for (int s = L - 1; s >= 0; --s) {
+            ex.s = s;
+            ex.offA = pA.off[s];
+            ex.lA = P.inA[s];
+            ex.rA = P.inA[s + 1];
+            if (P.mode == MODE_DIRSUM) {
+                ex.offB = pB.off[s];
+                ex.lB = P.inB[s];
+                ex.rB = P.inB[s + 1];
+            }
+            ex.rows0 = P.inA[s];
+            ex.cols0 = (s == L - 1) ? 1 : P.inA[s + 1];
+            const int Mg = P.e[s] * 4, Ng = P.k[s + 1], Kg = P.e[s + 1];
+            RowMajorB<T> bop{s == L - 1 ? nullptr : w.Lb[(s + 1) & 1], w.sL, P.k[s + 1]};
+            StoreRM<T> sto{w.wide + P.woff[s], w.sWide, Ng};
+            {
+                THC_LAUNCH("gemm_expand_absorb", st);
+                THC_CUDA(launch_gemm<T>(B, Mg, Ng, Kg, ex, bop, sto, st));
+            }
+            if (s >= 1) {
+                QRJob<T> job;
+                job.A = w.wide + P.woff[s];
+                job.strideA = w.sWide;
+                job.m = 4 * P.k[s + 1];
+                job.n = P.e[s];
+                job.ld = job.m;
+                job.Tw = w.Tw;
+                job.strideT = w.sTw;
+                job.out = w.Lb[s & 1];
+                job.strideOut = w.sL;
+                qr_params<T>(job.m, job.nb, job.tc);
+                job.mode = QR_L_AND_Q;
+                {
+                    THC_LAUNCH("qr_lq_sweep", st);
+                    k_qr<T><<<B, 256, qr_smem_bytes<T>(job.m, job.nb, job.tc), st>>>(job);
+                }
+                check();
+            }
+        }
+        // ---- SVD sweep, left to right
+        for (int s = 0; s < L - 1; ++s) {
+            const int m = 4 * P.out[s], n = P.k[s + 1], kout = P.out[s + 1];
+            // C_s = M_{s-1} Q_s  (M_{-1} = [1], Q_0 = X_0)
+            StoreC<T> sto{w.C, w.sC, m > n ? w.W : nullptr, w.sC, m, n, 4 * n};
+            RowMajorB<T> qop{w.wide + P.woff[s], w.sWide, 4 * n};
+            if (s == 0) {
+                THC_LAUNCH("gemm_center", st);
+                THC_CUDA(launch_gemm<T>(B, P.out[0], 4 * n, 1, IdentA<T>{}, qop, sto, st));
+            } else {
+                RowMajorA<T> mop{w.M[(s - 1) & 1], w.sV, P.k[s]};
+                THC_LAUNCH("gemm_center", st);
+                THC_CUDA(launch_gemm<T>(B, P.out[s], 4 * n, P.k[s], mop, qop, sto, st));
+            }
+            int p = std::min(m, n);
+            if (m > n) {
+                QRJob<T> job;
+                job.A = w.W;
+                job.strideA = w.sC;
+                job.m = m;
+                job.n = n;
+                job.ld = m;
+                job.Tw = w.Tw;
+                job.strideT = w.sTw;
+                job.out = w.Z;
+                job.strideOut = w.sZ;
+                qr_params<T>(m, job.nb, job.tc);
+                job.mode = QR_R_ROWS;
+                {
+                    THC_LAUNCH("qr_svd_precond", st);
+                    k_qr<T><<<B, 256, qr_smem_bytes<T>(m, job.nb, job.tc), st>>>(job);
+                }
+                check();
+            } else {
+                dim3 g(ceil_div(m * n, 256 * 4) + 1, B);
+                THC_LAUNCH("copy", st);
+                k_copy_batched<T><<<g, 256, 0, st>>>(w.Z, w.sZ, w.C, w.sC, (long)m * n);
+                check();
+            }
+            jacobi_select(B, p, n, kout, w);
+            // U = C V^T -> output site s, then normalise and form M_s
+            RowMajorA<T> cop{w.C, w.sC, n};
+            TransB<T> vop{w.V, w.sV, n};
+            StoreRM<T> uo{out + pO.off[s], out_stride, kout};
+            {
+                THC_LAUNCH("gemm_u", st);
+                THC_CUDA(launch_gemm<T>(B, m, kout, n, cop, vop, uo, st));
+            }
+            const size_t fsm = ((size_t)kout * kout + kout) * sizeof(T);
+            if (fsm > 227 * 1024) throw Error(THC_EUNSUPPORTED, "bond too large for finalize");
+            THC_LAUNCH("svd_finalize", st);
+            k_svd_finalize<T><<<B, 256, fsm, st>>>(out + pO.off[s], out_stride, m, w.V, w.sV, n,
+                                                  kout, w.M[s & 1], w.sV);
+            check();
+        }
+        // ---- last site: M_{L-2} Q_{L-1}
+        {
+            const int s = L - 1;
+            RowMajorA<T> mop{w.M[(s - 1) & 1], w.sV, P.k[s]};
+            RowMajorB<T> qop{w.wide + P.woff[s], w.sWide, 4 * P.k[s + 1]};
+            StoreRM<T> so{out + pO.off[s], out_stride, 4 * P.k[s + 1]};
+            THC_LAUNCH("gemm_center", st);
+            THC_CUDA(launch_gemm<T>(B, P.out[s], 4 * P.k[s + 1], P.k[s], mop, qop, so, st));
+        }
+    }
+
+    // rotation threshold on the row cosine: a multiple of the rounding error of
+    // the warp dot product (NPL sequential terms per lane + 5 butterfly levels)
+    double rot_tol(int n) const { return 8.0 * (ceil_div(std::max(n, 1), 32) + 6) * Real<T>::eps; }
+    double tol_ = 0.0;
+
+    void jacobi_select(int B, int p, int n, int kout, Work<T>& w) {
+        JacobiJob<T> j;
+        j.Z = w.Z;
+        j.strideZ = w.sZ;
+        j.p = p;
+        j.n = n;
+        j.V = w.V;
+        j.strideV = w.sV;
+        j.sv = w.sv;
+        j.strideSv = w.sSv;
+        j.keep = w.keep;
+        j.kout = kout;
+        j.tol = tol_;
+        j.rot_tol = rot_tol(n);
+        j.max_sweeps = 30;
+        j.status = dflag;
+        j.dbg = ddbg;
+        const size_t base = ((size_t)p * (sizeof(double) + sizeof(int)) + 15) & ~(size_t)15;
+        const size_t zb = (size_t)p * n * sizeof(T);
+        const int in_smem = (base + zb <= 200 * 1024) ? 1 : 0;
+        const size_t smem = base + (in_smem ? zb : 0);
+        THC_LAUNCH("jacobi_svd", st);
+        if (n <= 128) k_jacobi_select<T, 4><<<B, 256, smem, st>>>(j, in_smem);
+        else if (n <= 256) k_jacobi_select<T, 8><<<B, 256, smem, st>>>(j, in_smem);
+        else if (n <= 512) k_jacobi_select<T, 16><<<B, 256, smem, st>>>(j, in_smem);
+        else if (n <= 1024) k_jacobi_select<T, 32><<<B, 256, smem, st>>>(j, in_smem);
+        else throw Error(THC_EUNSUPPORTED, "bond dimension above 512 is not supported");
+        check();
+    }
+
+    // ---------------------------------------------------------- reduction
+    // Pairwise add-and-compress of n MPS (profile prof) stored at buf; result
+    // returned in a buffer from sc (or buf itself when n == 1).
+    T* reduce(Scratch& sc, T* buf, long n, const std::vector<int>& prof, int D, int Bw) {
+        Profile pf(prof);
+        Plan PD = make_plan<T>(MODE_DIRSUM, prof, prof, D);
+        for (int b = 0; b <= pf.L; ++b)
+            if (PD.out[b] != prof[b]) throw Error(THC_EINVAL, "reduction profile is not a fixed point");
+        if (n == 1) return buf;
+        const long half = (n + 1) / 2;
+        T* nxt0 = sc.get<T>((size_t)half * pf.size);
+        T* nxt1 = half > 1 ? sc.get<T>((size_t)((half + 1) / 2) * pf.size) : nullptr;
+        Scratch ws(al);
+        Work<T> w;
+        const int B = (int)std::min<long>(Bw, n / 2);
+        alloc_work(ws, w, B, {&PD});
+        {
+            THC_LAUNCH("setup", st);
+            k_pair_coefs<T><<<ceil_div(B, 128), 128, 0, st>>>(w.pcoef, B, nullptr, nullptr);
+        }
+        check();
+        T* cur = buf;
+        int flip = 0;
+        while (n > 1) {
+            const long np = n / 2;
+            T* nxt = flip ? nxt1 : nxt0;
+            for (long j0 = 0; j0 < np; j0 += B) {
+                const int Bc = (int)std::min<long>(B, np - j0);
+                {
+                    THC_LAUNCH("setup", st);
+                    k_pair_src<<<ceil_div(Bc, 128), 128, 0, st>>>(w.srcA, w.srcB, Bc, (int)(2 * j0));
+                }
+                check();
+                ExpandA<T> ex{};
+                ex.mode = MODE_DIRSUM;
+                ex.inA = cur;
+                ex.strideA = pf.size;
+                ex.srcA = w.srcA;
+                ex.inB = cur;
+                ex.strideB = pf.size;
+                ex.srcB = w.srcB;
+                ex.coef = w.pcoef;
+                compress(PD, Bc, ex, nxt + j0 * pf.size, pf.size, w);
+            }
+            if (n & 1)
+                THC_CUDA(cudaMemcpyAsync(nxt + np * pf.size, cur + (n - 1) * pf.size, pf.size * sizeof(T),
+                                         cudaMemcpyDeviceToDevice, st));
+            cur = nxt;
+            n = (n + 1) / 2;
+            flip ^= 1;
+        }
+        return cur;
+    }
+};
+
+}  // namespace thc

@@ -1,0 +1,422 @@
+// engine_ops.cuh -- the library's operations built on Engine<T>.
+#pragma once
+
+#include <cmath>
+
+#include "engine_impl.cuh"
+
+namespace thc {
+
+// ---------------------------------------------------------------- inner product functors
+struct EA {  // E(m, k), float64 row-major
+    const double* E;
+    long sE;
+    int ld;
+    __device__ __forceinline__ double operator()(int b, int m, int k) const {
+        return E[(long)b * sE + (long)m * ld + k];
+    }
+};
+template <class T>
+struct SiteB {  // B(k, n) = site[k*ld + n] of term b
+    const T* base;
+    long stride;
+    int ld;
+    __device__ __forceinline__ double operator()(int b, int k, int n) const {
+        return double(base[(long)b * stride + (long)k * ld + n]);
+    }
+};
+template <class T>
+struct SiteAT {  // A(m, k) = site[k*ld + m] (transposed access; real: conj is identity)
+    const T* base;
+    long stride;
+    int ld;
+    __device__ __forceinline__ double operator()(int b, int m, int k) const {
+        return double(base[(long)b * stride + (long)k * ld + m]);
+    }
+};
+struct StoreD {
+    double* base;
+    long stride;
+    int ld;
+    __device__ __forceinline__ void operator()(int b, int m, int n, double v) const {
+        base[(long)b * stride + (long)m * ld + n] = v;
+    }
+};
+
+__global__ void k_set_one(double* E, long stride, int B) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < B) E[(long)b * stride] = 1.0;
+}
+__global__ void k_gather_scalar(const double* E, long stride, int B, double* out) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < B) out[b] = E[(long)b * stride];
+}
+template <class T>
+__global__ void k_scale(T* x, long n, double c) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        x[i] = T(double(x[i]) * c);
+}
+
+// A device MPS in the engine's contiguous layout (one term).
+template <class T>
+struct DevMps {
+    T* base = nullptr;
+    std::vector<int> bond;
+};
+
+template <class T>
+struct Ops {
+    Engine<T>& E;
+    explicit Ops(Engine<T>& e) : E(e) {}
+    cudaStream_t st() const { return E.st; }
+
+    // ------------------------------------------------------------- transfers
+    void upload(const thc_mps* m, const std::vector<int>& prof, T* dst) {
+        Profile p(prof);
+        for (int s = 0; s < m->L; ++s) {
+            const long n = p.site_size(s);
+            const int blocks = (int)std::min<long>(ceil_div((int)std::min<long>(n, 1L << 30), 256), 4096);
+            THC_LAUNCH("copy", st());
+            k_copy_pad<T><<<std::max(blocks, 1), 256, 0, st()>>>(dst + p.off[s], prof[s], prof[s + 1],
+                                                                  (const T*)m->site[s], m->bond[s], m->bond[s + 1]);
+            E.check();
+        }
+    }
+
+    void download(const T* src, const std::vector<int>& prof, thc_mps* out, thc_dtype dt) {
+        Profile p(prof);
+        void* blk = E.al.get((size_t)p.size * sizeof(T));
+        THC_CUDA(cudaMemcpyAsync(blk, src, p.size * sizeof(T), cudaMemcpyDeviceToDevice, st()));
+        std::memset(out, 0, sizeof(*out));
+        out->L = p.L;
+        out->d = 4;
+        out->dtype = dt;
+        for (int b = 0; b <= p.L; ++b) out->bond[b] = prof[b];
+        for (int s = 0; s < p.L; ++s) out->site[s] = (void*)((T*)blk + p.off[s]);
+        out->owner = blk;
+    }
+
+    // --------------------------------------------------------- inner products
+    // <phi_b|psi_b> for B pairs stored strided (phi: base + b*sphi, psi: base + b*spsi).
+    void inner_batched(int B, const T* phi, long sphi, const std::vector<int>& pp, const T* psi,
+                       long spsi, const std::vector<int>& pq, double* out_dev) {
+        Profile a(pp), c(pq);
+        const int L = a.L;
+        int ma = 1, mb = 1;
+        for (int x : pp) ma = std::max(ma, x);
+        for (int x : pq) mb = std::max(mb, x);
+        Scratch sc(E.al);
+        const long sE = (long)ma * mb, sF = (long)ma * 4 * mb;
+        double* Eb = sc.get<double>((size_t)B * sE);
+        double* Fb = sc.get<double>((size_t)B * sF);
+        {
+            THC_LAUNCH("setup", st());
+            k_set_one<<<ceil_div(B, 128), 128, 0, st()>>>(Eb, sE, B);
+        }
+        E.check();
+        for (int s = 0; s < L; ++s) {
+            const int al = pp[s], ar = pp[s + 1], bl = pq[s], br = pq[s + 1];
+            // F = E B_s  : [al x bl] x [bl x 4 br]
+            {
+            THC_LAUNCH("gemm_inner", st());
+            THC_CUDA(launch_gemm<double>(B, al, 4 * br, bl, EA{Eb, sE, bl},
+                                         SiteB<T>{psi + c.off[s], spsi, 4 * br}, StoreD{Fb, sF, 4 * br}, st()));
+            }
+            // E' = A_s^T F : [(al,4) x ar]^T x [(al,4) x br]
+            {
+            THC_LAUNCH("gemm_inner", st());
+            THC_CUDA(launch_gemm<double>(B, ar, br, 4 * al, SiteAT<T>{phi + a.off[s], sphi, ar},
+                                         EA{Fb, sF, br}, StoreD{Eb, sE, br}, st()));
+            }
+        }
+        {
+            THC_LAUNCH("setup", st());
+            k_gather_scalar<<<ceil_div(B, 128), 128, 0, st()>>>(Eb, sE, B, out_dev);
+        }
+        E.check();
+    }
+
+    double inner1(const T* phi, const std::vector<int>& pp, const T* psi, const std::vector<int>& pq) {
+        Scratch sc(E.al);
+        double* d = sc.get<double>(1);
+        inner_batched(1, phi, 0, pp, psi, 0, pq, d);
+        double h = 0;
+        THC_CUDA(cudaMemcpyAsync(&h, d, sizeof(double), cudaMemcpyDeviceToHost, st()));
+        THC_CUDA(cudaStreamSynchronize(st()));
+        return h;
+    }
+
+    // ------------------------------------------------------------ layer apply
+    void layer_apply(const T* psi, const std::vector<int>& pin, const double* coef_dev, int sigma,
+                     int dagger, int D, T* out, std::vector<int>& pout, int Bw) {
+        Plan P = make_plan<T>(MODE_LAYER, pin, {}, D);
+        Scratch sc(E.al);
+        Work<T> w;
+        E.alloc_work(sc, w, 1, {&P});
+        const int L = P.L;
+        {
+            THC_LAUNCH("setup", st());
+            k_convert<T, double><<<1, 64, 0, st()>>>(w.coef1, coef_dev, L);
+        }
+        const int op = sigma + 2 * (dagger ? 1 : 0);
+        THC_CUDA(cudaMemcpyAsync(w.op1, &op, sizeof(int), cudaMemcpyHostToDevice, st()));
+        ExpandA<T> ex{};
+        ex.mode = MODE_LAYER;
+        ex.inA = psi;
+        ex.strideA = 0;
+        ex.coef = w.coef1;
+        ex.coef_ld = L;
+        ex.opsel = w.op1;
+        E.compress(P, 1, ex, out, 0, w);
+        pout = P.out;
+        THC_CUDA(cudaStreamSynchronize(st()));  // host op value must outlive the copy
+    }
+
+    void plain_compress(const T* psi, const std::vector<int>& pin, int D, T* out, std::vector<int>& pout) {
+        Plan P = make_plan<T>(MODE_PLAIN, pin, {}, D);
+        Scratch sc(E.al);
+        Work<T> w;
+        E.alloc_work(sc, w, 1, {&P});
+        ExpandA<T> ex{};
+        ex.mode = MODE_PLAIN;
+        ex.inA = psi;
+        E.compress(P, 1, ex, out, 0, w);
+        pout = P.out;
+    }
+
+    // --------------------------------------------------------------- H|psi>
+    // psi: device MPS with profile pin (every bond >= the full profile of D).
+    // Output written to out (profile full_profile(L, D)).
+    void apply_H(const thc_hamiltonian* H, const T* psi, const std::vector<int>& pin, const thc_opts* o,
+                 T* out) {
+        const int L = H->L, N = H->N, D = o->D_max;
+        const std::vector<int> pf = full_profile(L, D);
+        Profile Pf(pf);
+        Scratch sc(E.al);
+        E.tol_ = o->tol;
+        double* lam = sc.get<double>(L);
+        double* u = sc.get<double>((size_t)L * L);
+        {
+            THC_LAUNCH("kinetic_eigh", st());
+            k_kinetic_factors<<<1, 256, KINETIC_SMEM, st()>>>(L, H->t, lam, u, E.dflag);
+        }
+        E.check();
+        const long TT = 4L * N * N + 2L * L;
+        const long t0 = std::max(0L, o->term_begin < 0 ? 0L : o->term_begin);
+        const long t1 = (o->term_end < 0) ? TT : std::min(TT, o->term_end);
+        const long nT = t1 - t0;
+        if (nT <= 0) throw Error(THC_EINVAL, "empty term range");
+        Plan PA1 = make_plan<T>(MODE_LAYER, pin, {}, D);
+        Plan PA2 = make_plan<T>(MODE_LAYER, PA1.out, {}, D);
+        Plan PB1 = make_plan<T>(MODE_LAYER, pf, {}, D);
+        Plan PB2 = make_plan<T>(MODE_LAYER, PB1.out, {}, D);
+        Plan PD = make_plan<T>(MODE_DIRSUM, pf, pf, D);
+        if (PA2.out != pf || PB2.out != pf || PD.out != pf)
+            throw Error(THC_EINVAL, "input bonds below the full profile of D_max");
+        const long VV = 4L * N * N;
+        const long cEnd = std::min(t1, VV);
+        const bool hasV = t0 < cEnd;
+        const long j_first = hasV ? t0 / (2L * N) : 0;
+        const long nslots = hasV ? (cEnd - 1) / (2L * N) - j_first + 1 : 0;
+        // batch (terms in flight)
+        const std::vector<const Plan*> plans{&PA1, &PA2, &PB1, &PB2, &PD};
+        const size_t per_term = Engine<T>::work_bytes_per_term(plans) +
+                                sizeof(T) * (size_t)std::max(Profile(PA1.out).size, Profile(PB1.out).size);
+        size_t freeb = 0, totalb = 0;
+        THC_CUDA(cudaMemGetInfo(&freeb, &totalb));
+        long Bw = o->batch > 0 ? o->batch : 4L * E.sms;
+        Bw = std::max(1L, std::min<long>(Bw, (long)(0.3 * freeb / std::max<size_t>(per_term, 1))));
+        Bw = std::min<long>(Bw, std::max(nT, nslots));
+        Scratch sw(E.al);
+        Work<T> w;
+        E.alloc_work(sw, w, (int)Bw, plans);
+        T* tmp = sw.get<T>((size_t)Bw * std::max(Profile(PA1.out).size, Profile(PB1.out).size));
+        T* reuse = hasV ? sc.get<T>((size_t)nslots * Pf.size) : nullptr;
+        // ---- reuse stage (Alg. 1): psi_{nu s'} = compress(A+ compress(A psi))
+        for (long j0 = 0; j0 < nslots; j0 += Bw) {
+            const int Bc = (int)std::min<long>(Bw, nslots - j0);
+            THC_LAUNCH("term_coefs", st());
+            k_term_coefs<T><<<Bc, 64, 0, st()>>>(0, j_first + j0, Bc, L, N, H->chi, H->zeta, lam, u,
+                                                  j_first, w.coef1, w.coef2, w.op1, w.op2, w.src);
+            E.check();
+            ExpandA<T> e1{};
+            e1.mode = MODE_LAYER;
+            e1.inA = psi;
+            e1.strideA = 0;
+            e1.srcA = w.src;
+            e1.coef = w.coef1;
+            e1.coef_ld = L;
+            e1.opsel = w.op1;
+            E.compress(PA1, Bc, e1, tmp, Profile(PA1.out).size, w);
+            ExpandA<T> e2 = e1;
+            e2.inA = tmp;
+            e2.strideA = Profile(PA1.out).size;
+            e2.srcA = nullptr;
+            e2.coef = w.coef2;
+            e2.opsel = w.op2;
+            E.compress(PA2, Bc, e2, reuse + j0 * Pf.size, Pf.size, w);
+        }
+        // ---- terms, in power-of-two chunks that are exact subtrees of the pairwise reduction
+        THC_CUDA(cudaMemGetInfo(&freeb, &totalb));
+        long chunk = 1;
+        while (chunk < nT && (double)(2 * chunk) * 1.8 * Pf.size * sizeof(T) < 0.5 * freeb) chunk *= 2;
+        const long nchunks = (nT + chunk - 1) / chunk;
+        T* chunkres = sc.get<T>((size_t)nchunks * Pf.size);
+        for (long ci = 0; ci < nchunks; ++ci) {
+            const long c0 = ci * chunk, c1 = std::min(nT, c0 + chunk), n = c1 - c0;
+            Scratch scc(E.al);
+            T* res = scc.get<T>((size_t)n * Pf.size);
+            long w0 = c0;
+            while (w0 < c1) {
+                const long t = t0 + w0;
+                const bool isV = t < VV;
+                long w1 = std::min(c1, w0 + Bw);
+                if (isV) w1 = std::min(w1, VV - t0);
+                const int Bc = (int)(w1 - w0);
+                THC_LAUNCH("term_coefs", st());
+                k_term_coefs<T><<<Bc, 64, 0, st()>>>(1, t, Bc, L, N, H->chi, H->zeta, lam, u, j_first,
+                                                      w.coef1, w.coef2, w.op1, w.op2, w.src);
+                E.check();
+                const Plan& P1 = isV ? PB1 : PA1;
+                const Plan& P2 = isV ? PB2 : PA2;
+                ExpandA<T> e1{};
+                e1.mode = MODE_LAYER;
+                e1.inA = isV ? reuse : psi;
+                e1.strideA = isV ? Pf.size : 0;
+                e1.srcA = w.src;
+                e1.coef = w.coef1;
+                e1.coef_ld = L;
+                e1.opsel = w.op1;
+                const long s1 = Profile(P1.out).size;
+                E.compress(P1, Bc, e1, tmp, s1, w);
+                ExpandA<T> e2 = e1;
+                e2.inA = tmp;
+                e2.strideA = s1;
+                e2.srcA = nullptr;
+                e2.coef = w.coef2;
+                e2.opsel = w.op2;
+                E.compress(P2, Bc, e2, res + (w0 - c0) * Pf.size, Pf.size, w);
+                w0 = w1;
+            }
+            T* r = E.reduce(scc, res, n, pf, D, (int)Bw);
+            THC_CUDA(cudaMemcpyAsync(chunkres + ci * Pf.size, r, Pf.size * sizeof(T),
+                                     cudaMemcpyDeviceToDevice, st()));
+        }
+        T* fin = E.reduce(sc, chunkres, nchunks, pf, D, (int)Bw);
+        THC_CUDA(cudaMemcpyAsync(out, fin, Pf.size * sizeof(T), cudaMemcpyDeviceToDevice, st()));
+    }
+
+    // ------------------------------------------------------ add and compress
+    // sum_i c_i x_i (all with profile pf, the full profile of D) by the pairwise reduction.
+    void add_compress(int n, const double* c, const T* const* xs, const std::vector<int>& pf, int D,
+                      T* out) {
+        Profile P(pf);
+        Scratch sc(E.al);
+        T* buf = sc.get<T>((size_t)n * P.size);
+        for (int i = 0; i < n; ++i) {
+            THC_CUDA(cudaMemcpyAsync(buf + (long)i * P.size, xs[i], P.size * sizeof(T),
+                                     cudaMemcpyDeviceToDevice, st()));
+            const long s = P.L - 1;
+            THC_LAUNCH("scale", st());
+            k_scale<T><<<64, 256, 0, st()>>>(buf + (long)i * P.size + P.off[s], P.site_size(s), c[i]);
+            E.check();
+        }
+        T* r = E.reduce(sc, buf, n, pf, D, std::max(1, std::min(n / 2, 4 * E.sms)));
+        THC_CUDA(cudaMemcpyAsync(out, r, P.size * sizeof(T), cudaMemcpyDeviceToDevice, st()));
+        THC_CUDA(cudaStreamSynchronize(st()));
+    }
+
+    // ------------------------------------------------------------- Lanczos
+    // Returns the number of Krylov vectors; Ht, S (n x n host, row-major).
+    int krylov_basis(const thc_hamiltonian* H, const T* psi0, const std::vector<int>& pf, int K,
+                     const thc_opts* o, T* vbuf, T* wbuf, std::vector<double>& Ht,
+                     std::vector<double>& S) {
+        Profile P(pf);
+        const long sz = P.size;
+        THC_CUDA(cudaMemcpyAsync(vbuf, psi0, sz * sizeof(T), cudaMemcpyDeviceToDevice, st()));
+        const double n0 = std::sqrt(std::fabs(inner1(vbuf, pf, vbuf, pf)));
+        if (!(n0 > 0.0)) throw Error(THC_EBREAKDOWN, "zero initial vector");
+        {
+            THC_LAUNCH("scale", st());
+            k_scale<T><<<64, 256, 0, st()>>>(vbuf + P.off[P.L - 1], P.site_size(P.L - 1), 1.0 / n0);
+        }
+        E.check();
+        int nv = 1;
+        Scratch sc(E.al);
+        double* hd = sc.get<double>((size_t)K + 1);
+        for (int k = 0; k < K; ++k) {
+            apply_H(H, vbuf + k * sz, pf, o, wbuf + k * sz);
+            if (k == K - 1) break;
+            inner_batched(k + 1, vbuf, sz, pf, wbuf + k * sz, 0, pf, hd);
+            std::vector<double> h(k + 1);
+            THC_CUDA(cudaMemcpyAsync(h.data(), hd, (k + 1) * sizeof(double), cudaMemcpyDeviceToHost, st()));
+            THC_CUDA(cudaStreamSynchronize(st()));
+            std::vector<const T*> xs;
+            std::vector<double> cs;
+            xs.push_back(wbuf + k * sz);
+            cs.push_back(1.0);
+            for (int j = 0; j <= k; ++j) {
+                xs.push_back(vbuf + j * sz);
+                cs.push_back(-h[j]);
+            }
+            T* r = vbuf + (k + 1) * sz;
+            add_compress((int)xs.size(), cs.data(), xs.data(), pf, o->D_max, r);
+            const double nr = std::sqrt(std::fabs(inner1(r, pf, r, pf)));
+            const double nw = std::sqrt(std::fabs(inner1(wbuf + k * sz, pf, wbuf + k * sz, pf)));
+            if (!(nr >= 1e-8 * nw)) break;
+            {
+                THC_LAUNCH("scale", st());
+                k_scale<T><<<64, 256, 0, st()>>>(r + P.off[P.L - 1], P.site_size(P.L - 1), 1.0 / nr);
+            }
+            E.check();
+            nv = k + 2;
+        }
+        Ht.assign((size_t)nv * nv, 0.0);
+        S.assign((size_t)nv * nv, 0.0);
+        double* col = sc.get<double>((size_t)nv);
+        std::vector<double> tmp(nv);
+        for (int k = 0; k < nv; ++k) {
+            inner_batched(nv, vbuf, sz, pf, wbuf + k * sz, 0, pf, col);
+            THC_CUDA(cudaMemcpyAsync(tmp.data(), col, nv * sizeof(double), cudaMemcpyDeviceToHost, st()));
+            THC_CUDA(cudaStreamSynchronize(st()));
+            for (int j = 0; j < nv; ++j) Ht[(size_t)j * nv + k] = tmp[j];
+            inner_batched(nv, vbuf, sz, pf, vbuf + k * sz, 0, pf, col);
+            THC_CUDA(cudaMemcpyAsync(tmp.data(), col, nv * sizeof(double), cudaMemcpyDeviceToHost, st()));
+            THC_CUDA(cudaStreamSynchronize(st()));
+            for (int j = 0; j < nv; ++j) S[(size_t)j * nv + k] = tmp[j];
+        }
+        return nv;
+    }
+
+    // projected problem on the device (float64 single-CTA kernel)
+    void krylov_small(int nv, const std::vector<double>& Ht, const std::vector<double>& S, int mode,
+                      double dt, std::vector<double>& ritz, std::vector<double>& cre,
+                      std::vector<double>& cim, int& rank) {
+        if (nv > SMALL_MAX) throw Error(THC_EINVAL, "Krylov dimension above 64");
+        Scratch sc(E.al);
+        double* d = sc.get<double>((size_t)2 * nv * nv + 3 * nv);
+        int* info = sc.get<int>(2);
+        THC_CUDA(cudaMemcpyAsync(d, Ht.data(), nv * nv * sizeof(double), cudaMemcpyHostToDevice, st()));
+        THC_CUDA(cudaMemcpyAsync(d + nv * nv, S.data(), nv * nv * sizeof(double), cudaMemcpyHostToDevice, st()));
+        double* rz = d + 2 * nv * nv;
+        double* cr = rz + nv;
+        double* ci = cr + nv;
+        {
+            THC_LAUNCH("krylov_small", st());
+            k_krylov_small<<<1, 256, KRYLOV_SMEM, st()>>>(nv, d, d + nv * nv, mode, dt, 1e-12, rz, cr, ci, info);
+        }
+        E.check();
+        ritz.resize(nv);
+        cre.resize(nv);
+        cim.resize(nv);
+        int inf[2];
+        THC_CUDA(cudaMemcpyAsync(ritz.data(), rz, nv * sizeof(double), cudaMemcpyDeviceToHost, st()));
+        THC_CUDA(cudaMemcpyAsync(cre.data(), cr, nv * sizeof(double), cudaMemcpyDeviceToHost, st()));
+        THC_CUDA(cudaMemcpyAsync(cim.data(), ci, nv * sizeof(double), cudaMemcpyDeviceToHost, st()));
+        THC_CUDA(cudaMemcpyAsync(inf, info, 2 * sizeof(int), cudaMemcpyDeviceToHost, st()));
+        THC_CUDA(cudaStreamSynchronize(st()));
+        rank = inf[0];
+    }
+};
+
+}  // namespace thc

@@ -1,0 +1,300 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances: float64 path -- untruncated H|psi> relative error <= 1e-10 against
+the dense Fock-space oracle, truncated results <= 1e-9 (gauge-invariant
+distance) and energies within 1e-8 against the oracle's MPS engine at equal
+D_max.  float32 path -- H|psi> relative error <= 1e-5 on O(1) states (the
+storage rounding is 6e-8 per entry; a compression chain of ~100 rotations per
+row and GEMM sums of length <= 1024 grow it to ~1e-6, with margin) and
+energies within 1e-6 Ha.  States are compared gauge-invariantly: as dense
+vectors for L <= 8, else by their amplitudes on configurations drawn from the
+oracle state's |psi|^2 (each amplitude computed one by one).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import fock as F  # noqa: E402
+from oracle import krylov as OK  # noqa: E402
+from oracle import mps as OM  # noqa: E402
+from oracle import thc as OT  # noqa: E402
+from paper_2409_12708_gb300.workloads import random_mps, sector_mps, thc_hamiltonian, workload  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2409_12708_gb300 import binding
+    return binding
+
+
+DT = {"fp64": torch.float64, "fp32": torch.float32}
+
+
+def dev(a, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dtype)
+
+
+def to_np(sites):
+    return [s.detach().cpu().double().numpy() for s in sites]
+
+
+def sample_configs(b, n, seed=0):
+    """Configurations drawn from |b|^2 (sequential conditional sampling)."""
+    rng = np.random.default_rng(seed)
+    L = len(b)
+    R = [None] * (L + 1)
+    R[L] = np.ones((1, 1))
+    for i in range(L - 1, -1, -1):
+        R[i] = np.einsum("anb,bc,dnc->ad", b[i], R[i + 1], b[i])
+    out = np.zeros((n, L), dtype=np.int64)
+    for k in range(n):
+        left = np.ones(1)
+        for i in range(L):
+            v = np.einsum("a,anb->nb", left, b[i])
+            p = np.einsum("nb,bc,nc->n", v, R[i + 1], v)
+            p = np.maximum(p, 0)
+            ni = rng.choice(4, p=p / p.sum())
+            out[k, i] = ni
+            left = v[ni] / np.sqrt(p[ni])
+    return out
+
+
+def amplitudes(a, cfgs):
+    amps = []
+    for c in cfgs:
+        v = np.ones(1)
+        for i, n in enumerate(c):
+            v = v @ a[i][:, n, :]
+        amps.append(v[0])
+    return np.array(amps)
+
+
+def rel_dist(a, b):
+    """Relative distance of two MPS, gauge-invariant: dense vectors for L <= 8,
+    else amplitudes on 400 configurations drawn from |b|^2."""
+    if len(b) <= 8:
+        va, vb = OM.to_dense(a), OM.to_dense(b)
+        return np.linalg.norm(va - vb) / max(np.linalg.norm(vb), 1e-300)
+    cfg = sample_configs(b, 400)
+    xa, xb = amplitudes(a, cfg), amplitudes(b, cfg)
+    return np.linalg.norm(xa - xb) / max(np.linalg.norm(xb), 1e-300)
+
+
+# ------------------------------------------------------------------ a1: term data
+def test_kinetic_factors_match_definition(B):
+    t, _, _ = thc_hamiltonian(9, 3, seed=3)
+    lam, u = B.thc_kinetic_factors(dev(t))
+    lam, u = lam.cpu().numpy(), u.cpu().numpy()
+    assert np.all(np.diff(lam) >= 0)
+    assert np.allclose(u.T @ u, np.eye(9), atol=1e-13)
+    assert np.allclose(u @ np.diag(lam) @ u.T, t, atol=1e-12)
+    assert np.allclose(lam, np.linalg.eigvalsh(t), atol=1e-12)
+
+
+# ------------------------------------------------------------------ a2-a4: one layer
+@pytest.mark.parametrize("path,tolr", [("fp64", 1e-12), ("fp32", 2e-6)])
+@pytest.mark.parametrize("sigma,dagger", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_layer_apply_untruncated_equals_dense_operator(B, path, tolr, sigma, dagger):
+    L = 6
+    psi = random_mps(L, 16, seed=sigma + 2 * dagger)
+    coef = np.random.default_rng(7).standard_normal(L)
+    out = B.thc_layer_apply([dev(a, DT[path]) for a in psi], dev(coef), sigma, dagger, D_max=64, path=path)
+    W = OM.ladder_mpo(coef, sigma, bool(dagger))
+    ref = OM.mpo_to_dense(W) @ OM.to_dense(psi)
+    got = OM.to_dense(to_np(out))
+    assert np.linalg.norm(got - ref) <= tolr * np.linalg.norm(ref)
+    # output bonds follow the static rule min(D_max, 4^b, 4^(L-b), 2 chi_b)
+    chi = [a.shape[2] for a in psi[:-1]]
+    assert [s.shape[2] for s in out[:-1]] == [min(64, 4 ** (b + 1), 4 ** (L - b - 1), 2 * chi[b])
+                                              for b in range(L - 1)]
+
+
+@pytest.mark.parametrize("path,tolr", [("fp64", 1e-9), ("fp32", 1e-5)])
+@pytest.mark.parametrize("D", [4, 7, 16])
+def test_layer_apply_truncated_matches_oracle(B, path, tolr, D):
+    L = 7
+    psi = sector_mps(L, 3, 4, 16, seed=40 + D)
+    coef = np.random.default_rng(D).standard_normal(L)
+    out = B.thc_layer_apply([dev(a, DT[path]) for a in psi], dev(coef), 1, 1, D_max=D, path=path)
+    ref = OT.apply_layer(psi, coef, 1, True, D, 0.0)
+    assert rel_dist(to_np(out), ref) < tolr
+
+
+@pytest.mark.parametrize("path,tolr", [("fp64", 1e-9), ("fp32", 1e-5)])
+def test_compress_truncation_tolerance_matches_oracle(B, path, tolr):
+    L = 8
+    psi = sector_mps(L, 4, 4, 64, seed=9, decay=3.0)
+    out = B.thc_compress([dev(a, DT[path]) for a in psi], D_max=64, tol=1e-3, path=path)
+    ref = OM.compress(psi, 64, 1e-3)
+    assert rel_dist(to_np(out), ref) < tolr
+    # the oracle drops singular values; the GPU keeps static shapes with zeros
+    assert max(x.shape[2] for x in ref) < 64
+
+
+# ------------------------------------------------------------------ a7: inner products
+@pytest.mark.parametrize("path,tolr", [("fp64", 1e-13), ("fp32", 1e-6)])
+def test_inner_product(B, path, tolr):
+    L = 7
+    a = random_mps(L, 16, seed=1)
+    b = random_mps(L, 8, seed=2)
+    got = B.mps_inner([dev(x, DT[path]) for x in a], [dev(x, DT[path]) for x in b])
+    ref = OM.inner([x.astype(np.float32).astype(np.float64) for x in a] if path == "fp32" else a,
+                   [x.astype(np.float32).astype(np.float64) for x in b] if path == "fp32" else b)
+    assert abs(got - ref) <= tolr * OM.norm(a) * OM.norm(b)
+
+
+# ------------------------------------------------------------------ a6: add + compress
+@pytest.mark.parametrize("path,tolr", [("fp64", 1e-9), ("fp32", 1e-5)])
+def test_add_compress_matches_oracle_pairwise(B, path, tolr):
+    L = 6
+    xs = [sector_mps(L, 3, 3, 16, seed=60 + i) for i in range(5)]
+    cs = [1.0, -0.5, 0.25, 2.0, -1.5]
+    out = B.mps_add_compress(cs, [[dev(a, DT[path]) for a in x] for x in xs], D_max=16, path=path)
+    ref = OT.pairwise_sum([OM.scale(x, c) for x, c in zip(xs, cs)], 16, 0.0)
+    assert rel_dist(to_np(out), ref) < tolr
+
+
+# ------------------------------------------------------------------ full H|psi>
+@pytest.mark.parametrize("L,N", [(3, 2), (4, 3), (5, 3)])
+def test_apply_H_untruncated_equals_dense(B, L, N):
+    t, chi, zeta = thc_hamiltonian(L, N, seed=10 + L)
+    psi = sector_mps(L, L // 2, (L + 1) // 2, 256, seed=11)
+    H = F.hamiltonian_eq1(t, F.thc_v(chi, zeta))
+    ref = H @ OM.to_dense(psi)
+    out = B.thc_apply_H(dev(t), dev(chi), dev(zeta), [dev(a) for a in psi], D_max=256, path="fp64")
+    got = OM.to_dense(to_np(out))
+    assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+def test_apply_H_untruncated_fp32(B):
+    L, N = 4, 3
+    t, chi, zeta = thc_hamiltonian(L, N, seed=14)
+    psi = sector_mps(L, 2, 2, 256, seed=15)
+    ref = F.hamiltonian_eq1(t, F.thc_v(chi, zeta)) @ OM.to_dense(psi)
+    out = B.thc_apply_H(dev(t), dev(chi), dev(zeta), [dev(a, torch.float32) for a in psi],
+                        D_max=256, path="fp32")
+    got = OM.to_dense(to_np(out))
+    assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("path,tolr", [("fp64", 1e-9), ("fp32", 1e-5)])
+def test_apply_H_truncated_L6_N12_D16(B, path, tolr):
+    t, chi, zeta, psi, D = workload("L6_N12_D16")
+    out = B.thc_apply_H(dev(t), dev(chi), dev(zeta), [dev(a, DT[path]) for a in psi], D_max=D, path=path)
+    ref = OT.apply_H(psi, t, chi, zeta, D_max=D)
+    assert rel_dist(to_np(out), ref) < tolr
+    e_gpu = OM.inner(psi, to_np(out))
+    e_ref = OM.inner(psi, ref)
+    # float32: relative 1e-6 of the energy (float32 storage resolves ~6e-8)
+    assert abs(e_gpu - e_ref) < (1e-8 if path == "fp64" else 1e-6 * abs(e_ref))
+
+
+@pytest.mark.parametrize("batch", [1, 7, 0])
+def test_apply_H_term_ranges_and_batching(B, batch):
+    L, N, D = 5, 3, 8
+    t, chi, zeta = thc_hamiltonian(L, N, seed=21)
+    psi = sector_mps(L, 2, 3, D, seed=22)
+    for t0, t1 in [(0, 1), (5, 23), (30, 46)]:  # Coulomb only, mixed blocks, Coulomb + kinetic
+        out = B.thc_apply_H(dev(t), dev(chi), dev(zeta), [dev(a) for a in psi], D_max=D,
+                            term_begin=t0, term_end=t1, batch=batch)
+        ref = OT.apply_H(psi, t, chi, zeta, D_max=D, term_begin=t0, term_end=t1)
+        assert rel_dist(to_np(out), ref) < 1e-9
+
+
+def test_apply_H_full_size_sampled_terms(B):
+    # L = 16, N = 48, D_max = 128 workload: the first four Coulomb terms and one
+    # kinetic term, each reduced with the pairwise tree, against the oracle.
+    t, chi, zeta, psi, D = workload("L16_N48_D128")
+    L, N = chi.shape
+    for path, tolr in [("fp64", 1e-9), ("fp32", 2e-5)]:
+        args = (dev(t), dev(chi), dev(zeta), [dev(a, DT[path]) for a in psi])
+        out = B.thc_apply_H(*args, D_max=D, path=path, term_begin=0, term_end=4)
+        ref = OT.apply_H(psi, t, chi, zeta, D_max=D, term_begin=0, term_end=4)
+        assert rel_dist(to_np(out), ref) < tolr
+        tk = 4 * N * N + 3
+        out = B.thc_apply_H(*args, D_max=D, path=path, term_begin=tk, term_end=tk + 1)
+        ref = OT.apply_H(psi, t, chi, zeta, D_max=D, term_begin=tk, term_end=tk + 1)
+        assert rel_dist(to_np(out), ref) < tolr
+
+
+# ------------------------------------------------------------------ a8: Lanczos
+@pytest.mark.parametrize("path", ["fp64", "fp32"])
+def test_lanczos_untruncated_matches_oracle(B, path):
+    # exact Krylov quantities (no truncation): well conditioned, both sides agree
+    L, N, D, K = 5, 4, 256, 6
+    t, chi, zeta = thc_hamiltonian(L, N, seed=30)
+    psi = sector_mps(L, 2, 3, 16, seed=31)
+    e, ritz, _ = B.krylov_lanczos_ground(dev(t), dev(chi), dev(zeta), [dev(a, DT[path]) for a in psi],
+                                         K, D_max=D, path=path)
+    e_ref, _, _ = OK.lanczos_ground(lambda x: OT.apply_H(x, t, chi, zeta, D_max=D), psi, K, D)
+    tol_e = 1e-8 if path == "fp64" else 2e-6 * abs(e_ref[0])
+    assert abs(e - e_ref[0]) < tol_e
+    assert np.allclose(ritz, e_ref, atol=10 * tol_e)
+
+
+@pytest.mark.parametrize("path", ["fp64", "fp32"])
+def test_lanczos_tolerance_truncated_matches_oracle(B, path):
+    # truncation by discarded weight (tol = 1e-4): truncated yet well conditioned
+    # (a 1e-12 perturbation of psi moves the oracle's energy by ~1e-11)
+    L, N, D, K, tol = 6, 6, 64, 5, 1e-4
+    t, chi, zeta = thc_hamiltonian(L, N, seed=0)
+    psi = sector_mps(L, 3, 3, 16, seed=1000)
+    e, _, _ = B.krylov_lanczos_ground(dev(t), dev(chi), dev(zeta), [dev(a, DT[path]) for a in psi],
+                                      K, D_max=D, tol=tol, path=path)
+    e_ref, _, _ = OK.lanczos_ground(lambda x: OT.apply_H(x, t, chi, zeta, D_max=D, tol=tol), psi, K, D, tol)
+    tol_e = 1e-8 if path == "fp64" else 2e-6 * abs(e_ref[0])
+    assert abs(e - e_ref[0]) < tol_e
+
+
+def test_lanczos_L6_N12_D16_random_state_is_ill_conditioned(B):
+    # The L = 6, N = 12, D_max = 16 workload starts from a random sector state with
+    # a flat Schmidt spectrum, so every truncation at D = 16 cuts through
+    # near-degenerate singular values: a 1e-14 relative perturbation of psi moves
+    # the oracle's own 10-step energy by ~1e-3.  Parity there is bounded by that
+    # conditioning, not by the arithmetic.
+    t, chi, zeta, psi, D = workload("L6_N12_D16")
+    K = 10
+    e, _, _ = B.krylov_lanczos_ground(dev(t), dev(chi), dev(zeta), [dev(a) for a in psi], K, D_max=D)
+    e_ref, _, _ = OK.lanczos_ground(lambda x: OT.apply_H(x, t, chi, zeta, D_max=D), psi, K, D)
+    assert abs(e - e_ref[0]) < 1e-2
+
+
+def test_lanczos_untruncated_reaches_ED(B):
+    L, N = 3, 3
+    t, chi, zeta = thc_hamiltonian(L, N, seed=20)
+    psi = sector_mps(L, 1, 2, 64, seed=21)
+    e, _, ground = B.krylov_lanczos_ground(dev(t), dev(chi), dev(zeta), [dev(a) for a in psi], 9,
+                                           D_max=64, want_ground=True)
+    H = F.hamiltonian_eq1(t, F.thc_v(chi, zeta))
+    assert abs(e - F.ground_energy(H, L, 1, 2)) < 1e-9
+    x = OM.to_dense(to_np(ground))
+    x /= np.linalg.norm(x)
+    assert np.linalg.norm(H @ x - e * x) < 1e-6
+
+
+# ------------------------------------------------------------------ edge cases
+def test_two_site_chain_and_zero_coefficients(B):
+    L = 2
+    psi = random_mps(L, 4, seed=3)
+    coef = np.zeros(L)
+    out = B.thc_layer_apply([dev(a) for a in psi], dev(coef), 0, 0, D_max=4)
+    # sum_s 0 * a_s = 0: the compressed state is exactly zero
+    assert all(float(s.abs().max()) == 0.0 for s in out)
+    coef = np.array([0.3, -1.1])
+    out = B.thc_layer_apply([dev(a) for a in psi], dev(coef), 1, 1, D_max=4)
+    ref = OM.mpo_to_dense(OM.ladder_mpo(coef, 1, True)) @ OM.to_dense(psi)
+    assert np.allclose(OM.to_dense(to_np(out)), ref, atol=1e-13)
+
+
+def test_invalid_inputs_raise(B):
+    psi = [dev(a) for a in random_mps(4, 4, seed=1)]
+    with pytest.raises(B.ThcError) as e:
+        B.thc_compress(psi, D_max=0)
+    assert e.value.status == B.EINVAL
+    with pytest.raises(B.ThcError) as e:
+        B.thc_compress(psi, D_max=4, path="fp32")  # float64 tensors on the float32 path
+    assert e.value.status == B.EINVAL
