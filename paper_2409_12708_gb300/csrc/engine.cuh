@@ -206,11 +206,12 @@ struct Plan {
 
 template <class T>
 inline void qr_params(int m, int& nb, int& tc) {
-    nb = sizeof(T) == 8 ? 16 : 32;
-    tc = 8;
-    const size_t budget = 200 * 1024;
+    nb = sizeof(T) == 8 ? 16 : 32;  // panel width (at most one warp of reflectors)
+    tc = QR_TC;                     // trailing tile width
+    const size_t budget = 220 * 1024;
     while (nb > 4 && qr_smem_bytes<T>(m, nb, tc) > budget) nb /= 2;
-    while (tc > 2 && qr_smem_bytes<T>(m, nb, tc) > budget) tc /= 2;
+    if (qr_smem_bytes<T>(m, nb, tc) > budget)
+        throw Error(THC_EUNSUPPORTED, "QR column length too large for shared memory");
 }
 
 template <class T>

@@ -22,6 +22,8 @@ struct Work {
     T *V = nullptr, *M[2] = {nullptr, nullptr}, *Tw = nullptr;
     double* sv = nullptr;
     int* keep = nullptr;
+    int* perm = nullptr;  // column order of C for the pivoted preconditioning QR
+    long sPerm = 0;
     // per-term layer data
     T *coef1 = nullptr, *coef2 = nullptr, *pcoef = nullptr;
     int *op1 = nullptr, *op2 = nullptr, *src = nullptr, *srcA = nullptr, *srcB = nullptr;
@@ -68,6 +70,7 @@ struct Engine {
         opt_in(k_jacobi_select<T, 16>, big);
         opt_in(k_jacobi_select<T, 32>, big);
         opt_in(k_svd_finalize<T>, big);
+        opt_in(k_colsort<T>, big);
         opt_in(k_kinetic_factors, (int)KINETIC_SMEM);
         opt_in(k_krylov_small, (int)KRYLOV_SMEM);
     }
@@ -106,6 +109,10 @@ struct Engine {
         w.Tw = sc.get<T>((size_t)B * w.sTw);
         w.sv = sc.get<double>((size_t)B * w.sSv);
         w.keep = sc.get<int>((size_t)B);
+        long maxN = 1;
+        for (auto* p : plans) maxN = std::max<long>(maxN, p->maxN);
+        w.sPerm = maxN;
+        w.perm = sc.get<int>((size_t)B * maxN);
         const int L = plans.empty() ? 1 : plans[0]->L;
         w.coef1 = sc.get<T>((size_t)B * L);
         w.coef2 = sc.get<T>((size_t)B * L);
@@ -177,6 +184,7 @@ struct Engine {
                 job.strideOut = w.sL;
                 qr_params<T>(job.m, job.nb, job.tc);
                 job.mode = QR_L_AND_Q;
+                job.colmap = nullptr;
                 {
                     THC_LAUNCH("qr_lq_sweep", st);
                     k_qr<T><<<B, 256, qr_smem_bytes<T>(job.m, job.nb, job.tc), st>>>(job);
@@ -199,8 +207,16 @@ struct Engine {
                 THC_CUDA(launch_gemm<T>(B, P.out[s], 4 * n, P.k[s], mop, qop, sto, st));
             }
             int p = std::min(m, n);
+            const int* colmap = nullptr;
             if (m > n) {
+                {
+                    THC_LAUNCH("qr_svd_precond", st);
+                    k_colsort<T><<<B, 256, (size_t)n * sizeof(double), st>>>(w.W, w.sC, m, n, m, w.perm);
+                }
+                check();
+                colmap = w.perm;
                 QRJob<T> job;
+                job.colmap = colmap;
                 job.A = w.W;
                 job.strideA = w.sC;
                 job.m = m;
@@ -223,7 +239,7 @@ struct Engine {
                 k_copy_batched<T><<<g, 256, 0, st>>>(w.Z, w.sZ, w.C, w.sC, (long)m * n);
                 check();
             }
-            jacobi_select(B, p, n, kout, w);
+            jacobi_select(B, p, n, kout, w, colmap);
             // U = C V^T -> output site s, then normalise and form M_s
             RowMajorA<T> cop{w.C, w.sC, n};
             TransB<T> vop{w.V, w.sV, n};
@@ -255,7 +271,7 @@ struct Engine {
     double rot_tol(int n) const { return 8.0 * (ceil_div(std::max(n, 1), 32) + 6) * Real<T>::eps; }
     double tol_ = 0.0;
 
-    void jacobi_select(int B, int p, int n, int kout, Work<T>& w) {
+    void jacobi_select(int B, int p, int n, int kout, Work<T>& w, const int* colmap) {
         JacobiJob<T> j;
         j.Z = w.Z;
         j.strideZ = w.sZ;
@@ -272,10 +288,14 @@ struct Engine {
         j.max_sweeps = 30;
         j.status = dflag;
         j.dbg = ddbg;
+        j.colmap = colmap;
+        const size_t budget = 200 * 1024;
         const size_t base = ((size_t)p * (sizeof(double) + sizeof(int)) + 15) & ~(size_t)15;
         const size_t zb = (size_t)p * n * sizeof(T);
-        const int in_smem = (base + zb <= 200 * 1024) ? 1 : 0;
-        const size_t smem = base + (in_smem ? zb : 0);
+        const int in_smem = (base + zb <= budget) ? 1 : 0;
+        // blocked ordering: one shared-memory slot of 2*blk rows for the CTA
+        j.blk = (int)std::max<size_t>(1, std::min<size_t>(32, (budget - base) / (2 * (size_t)n * sizeof(T))));
+        const size_t smem = base + (in_smem ? zb : 2 * (size_t)j.blk * n * sizeof(T));
         THC_LAUNCH("jacobi_svd", st);
         if (n <= 128) k_jacobi_select<T, 4><<<B, 256, smem, st>>>(j, in_smem);
         else if (n <= 256) k_jacobi_select<T, 8><<<B, 256, smem, st>>>(j, in_smem);

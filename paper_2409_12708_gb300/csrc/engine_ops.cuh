@@ -235,9 +235,11 @@ struct Ops {
         // ---- reuse stage (Alg. 1): psi_{nu s'} = compress(A+ compress(A psi))
         for (long j0 = 0; j0 < nslots; j0 += Bw) {
             const int Bc = (int)std::min<long>(Bw, nslots - j0);
-            THC_LAUNCH("term_coefs", st());
-            k_term_coefs<T><<<Bc, 64, 0, st()>>>(0, j_first + j0, Bc, L, N, H->chi, H->zeta, lam, u,
-                                                  j_first, w.coef1, w.coef2, w.op1, w.op2, w.src);
+            {
+                THC_LAUNCH("term_coefs", st());
+                k_term_coefs<T><<<Bc, 64, 0, st()>>>(0, j_first + j0, Bc, L, N, H->chi, H->zeta, lam, u,
+                                                      j_first, w.coef1, w.coef2, w.op1, w.op2, w.src);
+            }
             E.check();
             ExpandA<T> e1{};
             e1.mode = MODE_LAYER;
@@ -273,9 +275,11 @@ struct Ops {
                 long w1 = std::min(c1, w0 + Bw);
                 if (isV) w1 = std::min(w1, VV - t0);
                 const int Bc = (int)(w1 - w0);
-                THC_LAUNCH("term_coefs", st());
-                k_term_coefs<T><<<Bc, 64, 0, st()>>>(1, t, Bc, L, N, H->chi, H->zeta, lam, u, j_first,
-                                                      w.coef1, w.coef2, w.op1, w.op2, w.src);
+                {
+                    THC_LAUNCH("term_coefs", st());
+                    k_term_coefs<T><<<Bc, 64, 0, st()>>>(1, t, Bc, L, N, H->chi, H->zeta, lam, u, j_first,
+                                                          w.coef1, w.coef2, w.op1, w.op2, w.src);
+                }
                 E.check();
                 const Plan& P1 = isV ? PB1 : PA1;
                 const Plan& P2 = isV ? PB2 : PA2;
@@ -317,8 +321,10 @@ struct Ops {
             THC_CUDA(cudaMemcpyAsync(buf + (long)i * P.size, xs[i], P.size * sizeof(T),
                                      cudaMemcpyDeviceToDevice, st()));
             const long s = P.L - 1;
-            THC_LAUNCH("scale", st());
-            k_scale<T><<<64, 256, 0, st()>>>(buf + (long)i * P.size + P.off[s], P.site_size(s), c[i]);
+            {
+                THC_LAUNCH("scale", st());
+                k_scale<T><<<64, 256, 0, st()>>>(buf + (long)i * P.size + P.off[s], P.site_size(s), c[i]);
+            }
             E.check();
         }
         T* r = E.reduce(sc, buf, n, pf, D, std::max(1, std::min(n / 2, 4 * E.sms)));

@@ -43,6 +43,9 @@ struct JacobiJob {
     int* status;       // OR of DEV_* flags
     double* dbg;       // [4]: p, n, rotations and max cosine of the last sweep of the
                        // first matrix that did not converge (written once)
+    int blk;           // row block of the blocked ordering (slot of 2*blk rows)
+    const int* colmap; // optional per-term column permutation (n ints, stride n): Z's
+                       // column c is column colmap[c] of C; V is written in C's order
 };
 
 // player at tournament position `pos` in round r (position 0 fixed)
@@ -50,66 +53,220 @@ __device__ __forceinline__ int rr_player(int pos, int r, int P2) {
     return pos == 0 ? 0 : ((pos - 1 + r) % (P2 - 1)) + 1;
 }
 
+// Rotate up to K independent pairs of rows at once (rows ra[i], rb[i], i < cnt)
+// so that every pair becomes orthogonal.  The K pairs are interleaved so their
+// loads, warp reductions and scalar chains overlap (instruction-level
+// parallelism hides the latencies that dominate one pair at a time).  The
+// rotation of each pair is decided and parametrised once (lane 0, in the
+// storage precision) and broadcast: every lane holds the same sums, and
+// float64 arithmetic is scarce on this part.  Returns the number of rotations.
+template <class T, int NPL, int K>
+__device__ __forceinline__ int rotate_pairs(T* const (&ra)[K], T* const (&rb)[K], int cnt, int n,
+                                            double rot_tol, double floor2, double& mycos) {
+    const int lane = threadIdx.x & 31;
+    T xa[K][NPL], xb[K][NPL];
+    T sm[K][3];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        sm[k][0] = sm[k][1] = sm[k][2] = T(0);
+#pragma unroll
+        for (int i = 0; i < NPL; ++i) {
+            const int c = lane + 32 * i;
+            const bool ok = k < cnt && c < n;
+            xa[k][i] = ok ? ra[k][c] : T(0);
+            xb[k][i] = ok ? rb[k][c] : T(0);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int i = 0; i < NPL; ++i) {
+            sm[k][0] += xa[k][i] * xa[k][i];
+            sm[k][1] += xb[k][i] * xb[k][i];
+            sm[k][2] += xa[k][i] * xb[k][i];
+        }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) sm[k][j] += __shfl_xor_sync(0xffffffffu, sm[k][j], o);
+    T cc[K], ss[K];
+    int rot = 0;  // bit k set: pair k rotates
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            cc[k] = T(1);
+            ss[k] = T(0);
+            const T al = sm[k][0], be = sm[k][1], ga = sm[k][2];
+            if (k < cnt && al > T(floor2) && be > T(floor2)) {
+                const T nab = sqrt(al) * sqrt(be);
+                const T ag = ga < T(0) ? -ga : ga;
+                mycos = fmax(mycos, (double)(ag / nab));
+                if (ag > T(rot_tol) * nab) {
+                    const T zeta = (be - al) / (T(2) * ga);
+                    const T az = zeta < T(0) ? -zeta : zeta;
+                    const T t = copysign(T(1), zeta) / (az + sqrt(T(1) + zeta * zeta));
+                    cc[k] = T(1) / sqrt(T(1) + t * t);
+                    ss[k] = cc[k] * t;
+                    rot |= 1 << k;
+                }
+            }
+        }
+    }
+    rot = __shfl_sync(0xffffffffu, rot, 0);
+    int nrot = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        if (!(rot >> k & 1)) continue;
+        const T c = __shfl_sync(0xffffffffu, cc[k], 0);
+        const T s = __shfl_sync(0xffffffffu, ss[k], 0);
+#pragma unroll
+        for (int i = 0; i < NPL; ++i) {
+            const int col = lane + 32 * i;
+            if (col < n) {
+                ra[k][col] = c * xa[k][i] - s * xb[k][i];
+                rb[k][col] = s * xa[k][i] + c * xb[k][i];
+            }
+        }
+        ++nrot;
+    }
+    return nrot;
+}
+
+// pairs per warp in flight: as many as keep the two rows of every pair within
+// 64 registers per lane (4 at most)
+template <class T, int NPL>
+struct PairsInFlight {
+    static constexpr int raw = 128 / (NPL * (int)sizeof(T));
+    static constexpr int value = raw < 1 ? 1 : (raw > 4 ? 4 : raw);
+};
+
 // Rows with ||z||^2 <= floor2 are numerically zero (below the rounding level of
 // the matrix they came from): they are not rotated, and the selection drops them.
+//
+// Round-robin ordering over all p rows held in shared memory: p/2 disjoint
+// pairs per round, JK of them per warp at a time.
 template <class T, int NPL>
-__device__ void jacobi_rows(T* Z, int p, int n, double rot_tol, double floor2, int max_sweeps,
-                            int* nrot_sh, unsigned long long* maxcos_sh, int* status, double* dbg) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+__device__ int jacobi_sweep_smem(T* Z, int p, int n, int r0_unused, double rot_tol, double floor2,
+                                 double& mycos) {
+    constexpr int JK = PairsInFlight<T, NPL>::value;
+    const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int P2 = p + (p & 1);
-    if (P2 < 2) return;
+    int myrot = 0;
+    for (int r = 0; r < P2 - 1; ++r) {
+        for (int pi0 = wid * JK; pi0 < P2 / 2; pi0 += nw * JK) {
+            T* ra[JK];
+            T* rb[JK];
+            int cnt = 0;
+#pragma unroll
+            for (int k = 0; k < JK; ++k) {
+                const int pi = pi0 + k;
+                int a = -1, b = -1;
+                if (pi < P2 / 2) {
+                    a = rr_player(pi, r, P2);
+                    b = rr_player(P2 - 1 - pi, r, P2);
+                }
+                const bool ok = a >= 0 && a < p && b < p;
+                // valid pairs first so that cnt counts them
+                ra[k] = Z;
+                rb[k] = Z;
+                if (ok) {
+                    ra[cnt] = Z + (long)a * n;
+                    rb[cnt] = Z + (long)b * n;
+                    ++cnt;
+                }
+            }
+            myrot += rotate_pairs<T, NPL, JK>(ra, rb, cnt, n, rot_tol, floor2, mycos);
+        }
+        __syncthreads();
+    }
+    return myrot;
+}
+
+// Blocked ordering for Z too large for shared memory (Z stays in global
+// memory, L2-resident).  Rows are grouped in blocks of bs.  A sweep first
+// orthogonalises every block internally (round-robin inside the block), then
+// visits every pair of blocks once (round-robin over blocks); for a visited
+// pair (A, B) the CTA copies both blocks to shared memory and rotates the bs^2
+// cross pairs in bs shift rounds, round s pairing A_i with B_{(i+s) mod bs}:
+// bs independent pairs per round, JK per warp.  Every pair of rows is rotated
+// exactly once per sweep, as in the cyclic method.
+template <class T, int NPL>
+__device__ int jacobi_sweep_blocked(T* Z, int p, int n, int bs, T* slot, double rot_tol, double floor2,
+                                    double& mycos) {
+    constexpr int JK = PairsInFlight<T, NPL>::value;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int wid = tid >> 5, nw = nt >> 5;
+    const int nbk = ceil_div(p, bs);
+    const int P2 = nbk + (nbk & 1);
+    int myrot = 0;
+    // intra-block pairs
+    for (int kb = 0; kb < nbk; ++kb) {
+        const int r0 = kb * bs, nr = min(bs, p - r0);
+        for (int i = tid; i < nr * n; i += nt) slot[i] = Z[(long)r0 * n + i];
+        __syncthreads();
+        myrot += jacobi_sweep_smem<T, NPL>(slot, nr, n, 0, rot_tol, floor2, mycos);
+        for (int i = tid; i < nr * n; i += nt) Z[(long)r0 * n + i] = slot[i];
+        __syncthreads();
+    }
+    // cross-block pairs
+    for (int rr = 0; rr < P2 - 1; ++rr) {
+        for (int bp = 0; bp < P2 / 2; ++bp) {
+            const int A = rr_player(bp, rr, P2), Bk = rr_player(P2 - 1 - bp, rr, P2);
+            if (A >= nbk || Bk >= nbk) continue;
+            const int ra0 = A * bs, na = min(bs, p - ra0);
+            const int rb0 = Bk * bs, nb = min(bs, p - rb0);
+            T* sa = slot;
+            T* sb = slot + (size_t)bs * n;
+            for (int i = tid; i < na * n; i += nt) sa[i] = Z[(long)ra0 * n + i];
+            for (int i = tid; i < nb * n; i += nt) sb[i] = Z[(long)rb0 * n + i];
+            __syncthreads();
+            for (int sh = 0; sh < bs; ++sh) {
+                for (int i0 = wid * JK; i0 < bs; i0 += nw * JK) {
+                    T* ra[JK];
+                    T* rb[JK];
+                    int cnt = 0;
+#pragma unroll
+                    for (int k = 0; k < JK; ++k) {
+                        const int i = i0 + k, j = (i0 + k + sh) % bs;
+                        ra[k] = slot;
+                        rb[k] = slot;
+                        if (i < na && j < nb) {
+                            ra[cnt] = sa + (long)i * n;
+                            rb[cnt] = sb + (long)j * n;
+                            ++cnt;
+                        }
+                    }
+                    myrot += rotate_pairs<T, NPL, JK>(ra, rb, cnt, n, rot_tol, floor2, mycos);
+                }
+                __syncthreads();
+            }
+            for (int i = tid; i < na * n; i += nt) Z[(long)ra0 * n + i] = sa[i];
+            for (int i = tid; i < nb * n; i += nt) Z[(long)rb0 * n + i] = sb[i];
+            __syncthreads();
+        }
+    }
+    return myrot;
+}
+
+// Sweeps until a sweep applies no rotation (or the budget ends).  mode 1: Z in
+// shared memory; mode 0: Z in global memory with the blocked ordering.
+template <class T, int NPL>
+__device__ void jacobi_rows(T* Z, int p, int n, int in_smem, int bs, T* slot, double rot_tol, double floor2,
+                            int max_sweeps, int* nrot_sh, unsigned long long* maxcos_sh, int* status,
+                            double* dbg) {
+    const int lane = threadIdx.x & 31;
+    if (p < 2) return;
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         if (threadIdx.x == 0) {
             *nrot_sh = 0;
             *maxcos_sh = 0ull;
         }
         __syncthreads();
-        int myrot = 0;
         double mycos = 0.0;
-        for (int r = 0; r < P2 - 1; ++r) {
-            for (int pi = wid; pi < P2 / 2; pi += nw) {
-                int a = rr_player(pi, r, P2), bb = rr_player(P2 - 1 - pi, r, P2);
-                if (a >= p || bb >= p) continue;
-                T* za = Z + (long)a * n;
-                T* zb = Z + (long)bb * n;
-                T xa[NPL], xb[NPL];
-                T al = 0, be = 0, ga = 0;
-#pragma unroll
-                for (int i = 0; i < NPL; ++i) {
-                    const int c = lane + 32 * i;
-                    xa[i] = c < n ? za[c] : T(0);
-                    xb[i] = c < n ? zb[c] : T(0);
-                    al += xa[i] * xa[i];
-                    be += xb[i] * xb[i];
-                    ga += xa[i] * xb[i];
-                }
-                al = warp_sum(al);
-                be = warp_sum(be);
-                ga = warp_sum(ga);
-                const double da = al, db = be, dg = ga;
-                if (da <= floor2 || db <= floor2) continue;
-                const double nab = sqrt(da) * sqrt(db);  // no underflow of da*db
-                mycos = fmax(mycos, fabs(dg) / nab);
-                if (fabs(dg) <= rot_tol * nab) continue;
-                // rotation zeroing the (a,b) entry of the 2x2 Gram [[al, ga], [ga, be]]
-                const double zeta = (db - da) / (2.0 * dg);
-                const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                const double cs = 1.0 / sqrt(1.0 + t * t);
-                const T c = T(cs), s = T(cs * t);
-#pragma unroll
-                for (int i = 0; i < NPL; ++i) {
-                    const int col = lane + 32 * i;
-                    if (col < n) {
-                        const T na = c * xa[i] - s * xb[i];
-                        const T nb = s * xa[i] + c * xb[i];
-                        za[col] = na;
-                        zb[col] = nb;
-                    }
-                }
-                ++myrot;
-            }
-            __syncthreads();
-        }
+        const int myrot = in_smem ? jacobi_sweep_smem<T, NPL>(Z, p, n, 0, rot_tol, floor2, mycos)
+                                  : jacobi_sweep_blocked<T, NPL>(Z, p, n, bs, slot, rot_tol, floor2, mycos);
         if (lane == 0 && myrot) atomicAdd(nrot_sh, myrot);
         if (lane == 0) atomicMax(maxcos_sh, (unsigned long long)__double_as_longlong(mycos));
         __syncthreads();
@@ -133,6 +290,8 @@ __device__ void jacobi_rows(T* Z, int p, int n, double rot_tol, double floor2, i
 // p doubles (sigma^2) and p ints (order).
 template <class T, int NPL>
 __global__ void __launch_bounds__(256) k_jacobi_select(JacobiJob<T> job, int z_in_smem) {
+    // z_in_smem: 1 = Z copied to shared memory; 0 = blocked ordering with Z in
+    // global memory and a shared-memory slot of 2*job.blk rows
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int nrot_sh;
     __shared__ int kkeep_sh;
@@ -145,8 +304,9 @@ __global__ void __launch_bounds__(256) k_jacobi_select(JacobiJob<T> job, int z_i
     int* order = reinterpret_cast<int*>(s2 + p);
     T* Zg = job.Z + (long)b * job.strideZ;
     T* Z = Zg;
+    T* after = reinterpret_cast<T*>(smem_raw + ((p * (sizeof(double) + sizeof(int)) + 15) & ~15));
     if (z_in_smem) {
-        Z = reinterpret_cast<T*>(smem_raw + ((p * (sizeof(double) + sizeof(int)) + 15) & ~15));
+        Z = after;
         for (int i = tid; i < p * n; i += nt) Z[i] = Zg[i];
         __syncthreads();
     }
@@ -159,8 +319,8 @@ __global__ void __launch_bounds__(256) k_jacobi_select(JacobiJob<T> job, int z_i
     }
     const double fro2 = block_sum(part, red);
     const double floor2 = Real<T>::eps * Real<T>::eps * fro2;
-    jacobi_rows<T, NPL>(Z, p, n, job.rot_tol, floor2, job.max_sweeps, &nrot_sh, &maxcos_sh, job.status,
-                        job.dbg);
+    jacobi_rows<T, NPL>(Z, p, n, z_in_smem, job.blk, after, job.rot_tol, floor2, job.max_sweeps, &nrot_sh,
+                        &maxcos_sh, job.status, job.dbg);
     __syncthreads();
     // squared row norms in float64
     for (int r = wid; r < p; r += nw) {
@@ -220,8 +380,9 @@ __global__ void __launch_bounds__(256) k_jacobi_select(JacobiJob<T> job, int z_i
         }
         if (lane == 0) sv[j] = row >= 0 ? sig : 0.0;
         const double inv = row >= 0 ? 1.0 / sig : 0.0;
+        const int* cm = job.colmap ? job.colmap + (long)b * n : nullptr;
         for (int c = lane; c < n; c += 32)
-            V[(long)j * n + c] = row >= 0 ? T(Z[(long)row * n + c] * inv) : T(0);
+            V[(long)j * n + (cm ? cm[c] : c)] = row >= 0 ? T(Z[(long)row * n + c] * inv) : T(0);
     }
 }
 

@@ -32,71 +32,101 @@ struct QRJob {
     long strideOut;
     int nb, tc;    // panel width, trailing tile width
     int mode;
+    const int* colmap;  // optional per-term column permutation (n ints, stride n):
+                        // logical column c is stored in physical column colmap[c]
 };
 
 __host__ __device__ inline int qr_ldp(int m) { return m | 1; }  // odd stride: conflict-free
+
+#define QCOL(c) (cm ? cm[(c)] : (c))
 
 __host__ __device__ inline int qr_gsize(int nb, int tc) { return nb * (tc > nb ? tc : nb); }
 
 template <class T>
 __host__ inline size_t qr_smem_bytes(int m, int nb, int tc) {
     return 64 * sizeof(double) + (size_t)(nb + tc) * qr_ldp(m) * sizeof(T) +
-           (size_t)nb * nb * sizeof(T) + (size_t)qr_gsize(nb, tc) * sizeof(T);
+           (size_t)nb * nb * sizeof(T) + (size_t)qr_gsize(nb, tc) * sizeof(T) +
+           (size_t)8 * 32 * tc * sizeof(T);
 }
 
 // Apply (H_p0 ... H_{p0+pw-1})^T (transpose=true, factorisation) or
 // H_p0 ... H_{p0+pw-1} (transpose=false, forming Q) to columns [c_begin, c_end)
-// of A, rows [p0, m).  P holds the panel's V (local rows), Tm its T matrix.
-template <class T>
+// of A, rows [p0, m).  P holds the panel's V (local rows, column i at
+// P + i*ldp, unit diagonal implicit), Tm its T matrix.  Tiles of TC columns go
+// through shared memory Y (column-major, stride ldp):
+//   G = V^T Y : lane i of every warp owns row i of G (TC accumulators), the 8
+//               warps split the rows of Y and their partial sums meet in Gp;
+//   G <- T^T G (or T G), all threads, one column entry each;
+//   Y -= V G  : each thread owns ROWS_PER_T rows of the tile and all TC columns.
+constexpr int QR_TC = 16;
+
+template <class T, int TC>
 __device__ void qr_block_apply(T* A, int ld, int m, int p0, int pw, int c_begin, int c_end,
-                               const T* P, int ldp, const T* Tm, int nbT, T* Y, T* G, int tc,
-                               bool transpose) {
+                               const T* P, int ldp, const T* Tm, int nbT, T* Y, T* G, T* Gp,
+                               bool transpose, const int* cm) {
     const int R = m - p0;
     const int tid = threadIdx.x, nt = blockDim.x;
-    for (int c0 = c_begin; c0 < c_end; c0 += tc) {
-        const int tcn = min(tc, c_end - c0);
-        // stage the tile
-        for (int i = tid; i < tcn * R; i += nt) {
+    const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+    for (int c0 = c_begin; c0 < c_end; c0 += TC) {
+        const int tcn = min(TC, c_end - c0);
+        for (int i = tid; i < TC * R; i += nt) {
             const int c = i / R, r = i % R;
-            Y[c * ldp + r] = A[(long)(c0 + c) * ld + p0 + r];
+            Y[c * ldp + r] = c < tcn ? A[(long)QCOL(c0 + c) * ld + p0 + r] : T(0);
         }
         __syncthreads();
-        // G = V^T Y  (pw x tcn)
-        for (int o = tid; o < pw * tcn; o += nt) {
-            const int i = o % pw, c = o / pw;
-            const T* v = P + i * ldp;
-            const T* y = Y + c * ldp;
-            T s = y[i];
-            for (int r = i + 1; r < R; ++r) s += v[r] * y[r];
-            G[i * tc + c] = s;
+        // partial G over this warp's rows
+        {
+            T acc[TC];
+#pragma unroll
+            for (int c = 0; c < TC; ++c) acc[c] = T(0);
+            const int i = lane;
+            if (i < pw) {
+                const T* v = P + i * ldp;
+                const int rs = ceil_div(R, nw);
+                const int r0 = wid * rs, r1 = min(R, r0 + rs);
+                for (int r = max(r0, i); r < r1; ++r) {
+                    const T vr = (r == i) ? T(1) : v[r];
+#pragma unroll
+                    for (int c = 0; c < TC; ++c) acc[c] += vr * Y[c * ldp + r];
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < TC; ++c) Gp[(wid * 32 + lane) * TC + c] = acc[c];
+        }
+        __syncthreads();
+        for (int o = tid; o < pw * TC; o += nt) {
+            const int i = o / TC, c = o % TC;
+            T s = 0;
+            for (int w = 0; w < nw; ++w) s += Gp[(w * 32 + i) * TC + c];
+            G[i * TC + c] = s;
         }
         __syncthreads();
         // G <- T^T G (factorisation) or T G (forming Q); T upper triangular
-        if (tid < tcn) {
-            const int c = tid;
-            T h[64];
-            for (int i = 0; i < pw; ++i) {
-                T s = 0;
-                if (transpose) {
-                    for (int l = 0; l <= i; ++l) s += Tm[l * nbT + i] * G[l * tc + c];
-                } else {
-                    for (int l = i; l < pw; ++l) s += Tm[i * nbT + l] * G[l * tc + c];
-                }
-                h[i] = s;
+        for (int o = tid; o < pw * TC; o += nt) {
+            const int i = o / TC, c = o % TC;
+            T s = 0;
+            if (transpose) {
+                for (int l = 0; l <= i; ++l) s += Tm[l * nbT + i] * G[l * TC + c];
+            } else {
+                for (int l = i; l < pw; ++l) s += Tm[i * nbT + l] * G[l * TC + c];
             }
-            for (int i = 0; i < pw; ++i) G[i * tc + c] = h[i];
+            Gp[i * TC + c] = s;
         }
         __syncthreads();
-        // Y -= V G
-        for (int i = tid; i < tcn * R; i += nt) {
-            const int c = i / R, r = i % R;
-            T s = 0;
+        // Y -= V G, written straight back to A
+        for (int r = tid; r < R; r += nt) {
+            T acc[TC];
+#pragma unroll
+            for (int c = 0; c < TC; ++c) acc[c] = T(0);
             const int top = min(r, pw - 1);
             for (int l = 0; l <= top; ++l) {
                 const T v = (l == r) ? T(1) : P[l * ldp + r];
-                s += v * G[l * tc + c];
+#pragma unroll
+                for (int c = 0; c < TC; ++c) acc[c] += v * Gp[l * TC + c];
             }
-            A[(long)(c0 + c) * ld + p0 + r] = Y[c * ldp + r] - s;
+#pragma unroll
+            for (int c = 0; c < TC; ++c)
+                if (c < tcn) A[(long)QCOL(c0 + c) * ld + p0 + r] = Y[c * ldp + r] - acc[c];
         }
         __syncthreads();
     }
@@ -111,11 +141,13 @@ __global__ void __launch_bounds__(256) k_qr(QRJob<T> job) {
     const int ldp = qr_ldp(m);
     T* A = job.A + (long)b * job.strideA;
     T* Tw = job.Tw + (long)b * job.strideT;
+    const int* cm = job.colmap ? job.colmap + (long)b * n : nullptr;
     double* red = reinterpret_cast<double*>(smem_raw);
     T* P = reinterpret_cast<T*>(smem_raw + 64 * sizeof(double));
     T* Y = P + (size_t)nb * ldp;
     T* Tm = Y + (size_t)tc * ldp;
     T* G = Tm + nb * nb;
+    T* Gp = G + qr_gsize(nb, tc);
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
 
@@ -124,26 +156,39 @@ __global__ void __launch_bounds__(256) k_qr(QRJob<T> job) {
         const int R = m - p0;
         for (int i = tid; i < pw * R; i += nt) {
             const int c = i / R, r = i % R;
-            P[c * ldp + r] = A[(long)(p0 + c) * ld + p0 + r];
+            P[c * ldp + r] = A[(long)QCOL(p0 + c) * ld + p0 + r];
         }
         __syncthreads();
         // --- unblocked factorisation of the panel in shared memory
         for (int j = 0; j < pw; ++j) {
             T* x = P + j * ldp;
+            // The squared norm is accumulated in float64: a reflector is orthogonal
+            // only if beta^2 = alpha^2 + ||x||^2 holds to working precision, and a
+            // float32 sum over ~10^3 entries misses that by ~1e-6, which then
+            // compounds through the sweeps.
             double part = 0.0;
             for (int r = j + 1 + tid; r < R; r += nt) part += (double)x[r] * (double)x[r];
             const double xn2 = block_sum(part, red);
-            const double alpha = (double)x[j];
-            double tau = 0.0;
-            if (xn2 > 0.0) {
-                const double beta = -copysign(sqrt(alpha * alpha + xn2), alpha);
-                tau = (beta - alpha) / beta;
-                const T scale = T(1.0 / (alpha - beta));
-                for (int r = j + 1 + tid; r < R; r += nt) x[r] *= scale;
-                __syncthreads();
-                if (tid == 0) x[j] = T(beta);
+            // reflector parameters: one thread (float64), broadcast through shared memory
+            if (tid == 0) {
+                const double alpha = (double)x[j];
+                double tau = 0.0, scale = 0.0;
+                if (xn2 > 0.0) {
+                    const double beta = -copysign(sqrt(alpha * alpha + xn2), alpha);
+                    tau = (beta - alpha) / beta;
+                    scale = 1.0 / (alpha - beta);
+                    x[j] = T(beta);
+                }
+                red[40] = tau;
+                red[41] = scale;
+                Tm[j * nb + j] = T(tau);
             }
-            if (tid == 0) Tm[j * nb + j] = T(tau);
+            __syncthreads();
+            const double tau = red[40];
+            if (tau != 0.0) {
+                const T scale = T(red[41]);
+                for (int r = j + 1 + tid; r < R; r += nt) x[r] *= scale;
+            }
             __syncthreads();
             // apply H_j^T to panel columns j+1 .. pw-1 (one warp per column)
             if (tau != 0.0) {
@@ -187,11 +232,11 @@ __global__ void __launch_bounds__(256) k_qr(QRJob<T> job) {
         for (int i = tid; i < nb * nb; i += nt) Tw[(p0 / nb) * nb * nb + i] = Tm[i];
         for (int i = tid; i < pw * R; i += nt) {
             const int c = i / R, r = i % R;
-            A[(long)(p0 + c) * ld + p0 + r] = P[c * ldp + r];
+            A[(long)QCOL(p0 + c) * ld + p0 + r] = P[c * ldp + r];
         }
         __syncthreads();
         // --- trailing update of columns p0+pw .. n-1
-        qr_block_apply(A, ld, m, p0, pw, p0 + pw, n, P, ldp, Tm, nb, Y, G, tc, true);
+        qr_block_apply<T, QR_TC>(A, ld, m, p0, pw, p0 + pw, n, P, ldp, Tm, nb, Y, G, Gp, true, cm);
     }
 
     // --- outputs
@@ -199,14 +244,14 @@ __global__ void __launch_bounds__(256) k_qr(QRJob<T> job) {
     if (job.mode == QR_R_ROWS) {
         for (int i = tid; i < n * n; i += nt) {
             const int r = i / n, c = i % n;
-            out[i] = (r <= c && r < kk) ? A[(long)c * ld + r] : T(0);
+            out[i] = (r <= c && r < kk) ? A[(long)QCOL(c) * ld + r] : T(0);
         }
         return;
     }
     // QR_L_AND_Q: L = R^T (n x kk)
     for (int i = tid; i < n * kk; i += nt) {
         const int r = i / kk, c = i % kk;
-        out[i] = (c <= r) ? A[(long)r * ld + c] : T(0);
+        out[i] = (c <= r) ? A[(long)QCOL(r) * ld + c] : T(0);
     }
     __syncthreads();
     // form Q in place, panels in reverse order
@@ -217,12 +262,12 @@ __global__ void __launch_bounds__(256) k_qr(QRJob<T> job) {
         const int R = m - p0;
         for (int i = tid; i < pw * R; i += nt) {
             const int c = i / R, r = i % R;
-            P[c * ldp + r] = A[(long)(p0 + c) * ld + p0 + r];
+            P[c * ldp + r] = A[(long)QCOL(p0 + c) * ld + p0 + r];
         }
         for (int i = tid; i < nb * nb; i += nt) Tm[i] = Tw[pi * nb * nb + i];
         __syncthreads();
         if (p0 + pw < kk)
-            qr_block_apply(A, ld, m, p0, pw, p0 + pw, kk, P, ldp, Tm, nb, Y, G, tc, false);
+            qr_block_apply<T, QR_TC>(A, ld, m, p0, pw, p0 + pw, kk, P, ldp, Tm, nb, Y, G, Gp, false, cm);
         // panel columns in place (unblocked, backwards)
         for (int j = pw - 1; j >= 0; --j) {
             const T tj = Tm[j * nb + j];
@@ -244,9 +289,38 @@ __global__ void __launch_bounds__(256) k_qr(QRJob<T> job) {
         }
         for (int i = tid; i < pw * m; i += nt) {
             const int c = i / m, r = i % m;
-            A[(long)(p0 + c) * ld + r] = (r < p0) ? T(0) : P[c * ldp + (r - p0)];
+            A[(long)QCOL(p0 + c) * ld + r] = (r < p0) ? T(0) : P[c * ldp + (r - p0)];
         }
         __syncthreads();
+    }
+}
+
+// Static column pivoting: perm[c] = index of the column with the c-th largest
+// norm (ties by index).  Ordering the columns by norm before the Householder QR
+// grades the rows of R, which cuts the number of one-sided Jacobi sweeps on R.
+// One CTA per term; A column-major (m x n, ld); dynamic smem: n doubles.
+template <class T>
+__global__ void __launch_bounds__(256) k_colsort(const T* A, long strideA, int m, int n, int ld, int* perm) {
+    extern __shared__ __align__(16) double cn[];
+    const int b = blockIdx.x;
+    A += (long)b * strideA;
+    perm += (long)b * n;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int c = wid; c < n; c += nw) {
+        double acc = 0.0;
+        for (int r = lane; r < m; r += 32) {
+            const double x = A[(long)c * ld + r];
+            acc += x * x;
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) cn[c] = acc;
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        const double v = cn[c];
+        int rank = 0;
+        for (int q = 0; q < n; ++q) rank += (cn[q] > v) || (cn[q] == v && q < c);
+        perm[rank] = c;
     }
 }
 
