@@ -76,16 +76,30 @@ struct Call {
     Call(void* stream, const thc_allocator* a)
         : E((cudaStream_t)stream, a), sc(E.al), ops(E) {
         E.dflag = sc.get<int>(1);
-        E.ddbg = sc.get<double>(4);
+        E.ddbg = sc.get<double>(8);
         THC_CUDA(cudaMemsetAsync(E.dflag, 0, sizeof(int), E.st));
-        THC_CUDA(cudaMemsetAsync(E.ddbg, 0, 4 * sizeof(double), E.st));
+        THC_CUDA(cudaMemsetAsync(E.ddbg, 0, 8 * sizeof(double), E.st));
     }
     thc_status finish() {
         int f = 0;
-        double d[4];
+        double d[8];
         THC_CUDA(cudaMemcpyAsync(&f, E.dflag, sizeof(int), cudaMemcpyDeviceToHost, E.st));
-        THC_CUDA(cudaMemcpyAsync(d, E.ddbg, 4 * sizeof(double), cudaMemcpyDeviceToHost, E.st));
+        THC_CUDA(cudaMemcpyAsync(d, E.ddbg, 8 * sizeof(double), cudaMemcpyDeviceToHost, E.st));
         THC_CUDA(cudaStreamSynchronize(E.st));
+        {
+            unsigned long long c[4];
+            std::memcpy(c, d + 4, sizeof(c));
+            auto& p = thc::profiler();
+            std::lock_guard<std::mutex> g(p.mu);
+            if (p.on) {  // sweep statistics ride along with the profile
+                auto& a = p.acc["jacobi_sweeps_all"];
+                a.first += (long)c[1];
+                a.second += (double)c[0];
+                auto& b = p.acc["jacobi_sweeps_p_ge_128"];
+                b.first += (long)c[3];
+                b.second += (double)c[2];
+            }
+        }
         if (f & thc::DEV_NONFINITE) return fail(THC_ENONFINITE, "non-finite value met in a decomposition");
         if (f & thc::DEV_SMALL_NONCONV) return fail(THC_ETIMEOUT, "small eigensolver sweep budget exhausted");
         if (f & thc::DEV_NONCONVERGED) {

@@ -22,6 +22,9 @@ struct Work {
     T *V = nullptr, *M[2] = {nullptr, nullptr}, *Tw = nullptr;
     double* sv = nullptr;
     int* keep = nullptr;
+    T* nu = nullptr;  // column norms of U (stride sSv)
+    T* F = nullptr;   // V V^T (stride sF)
+    long sF = 0;
     int* perm = nullptr;  // column order of C for the pivoted preconditioning QR
     long sPerm = 0;
     // per-term layer data
@@ -69,7 +72,6 @@ struct Engine {
         opt_in(k_jacobi_select<T, 8>, big);
         opt_in(k_jacobi_select<T, 16>, big);
         opt_in(k_jacobi_select<T, 32>, big);
-        opt_in(k_svd_finalize<T>, big);
         opt_in(k_colsort<T>, big);
         opt_in(k_kinetic_factors, (int)KINETIC_SMEM);
         opt_in(k_krylov_small, (int)KRYLOV_SMEM);
@@ -90,13 +92,15 @@ struct Engine {
             mx.maxKout = std::max(mx.maxKout, p->maxKout);
         }
         w.B = B;
-        w.sWide = std::max(1L, mx.wsize);
-        w.sL = std::max(1L, mx.maxL);
-        w.sC = std::max(1L, mx.maxC);
-        w.sZ = std::max(1L, mx.maxZ);
-        w.sV = std::max(1L, mx.maxV);
-        w.sTw = std::max(1L, mx.maxTw);
-        w.sSv = std::max(1L, mx.maxKout);
+        // per-term strides rounded up to 128 bytes: every term's matrices stay aligned
+        auto up = [](long x) { return (std::max(1L, x) + 31) / 32 * 32; };
+        w.sWide = up(mx.wsize);
+        w.sL = up(mx.maxL);
+        w.sC = up(mx.maxC);
+        w.sZ = up(mx.maxZ);
+        w.sV = up(mx.maxV);
+        w.sTw = up(mx.maxTw);
+        w.sSv = up(mx.maxKout);
         w.wide = sc.get<T>((size_t)B * w.sWide);
         w.Lb[0] = sc.get<T>((size_t)B * w.sL);
         w.Lb[1] = sc.get<T>((size_t)B * w.sL);
@@ -108,6 +112,9 @@ struct Engine {
         w.M[1] = sc.get<T>((size_t)B * w.sV);
         w.Tw = sc.get<T>((size_t)B * w.sTw);
         w.sv = sc.get<double>((size_t)B * w.sSv);
+        w.nu = sc.get<T>((size_t)B * w.sSv);
+        w.sF = up(mx.maxKout * mx.maxKout);
+        w.F = sc.get<T>((size_t)B * w.sF);
         w.keep = sc.get<int>((size_t)B);
         long maxN = 1;
         for (auto* p : plans) maxN = std::max<long>(maxN, p->maxN);
@@ -248,12 +255,23 @@ struct Engine {
                 THC_LAUNCH("gemm_u", st);
                 THC_CUDA(launch_gemm<T>(B, m, kout, n, cop, vop, uo, st));
             }
-            const size_t fsm = ((size_t)kout * kout + kout) * sizeof(T);
-            if (fsm > 227 * 1024) throw Error(THC_EUNSUPPORTED, "bond too large for finalize");
-            THC_LAUNCH("svd_finalize", st);
-            k_svd_finalize<T><<<B, 256, fsm, st>>>(out + pO.off[s], out_stride, m, w.V, w.sV, n,
-                                                  kout, w.M[s & 1], w.sV);
+            // normalise U's columns, then M = diag(nu) (I - F') V with F = V V^T
+            {
+                THC_LAUNCH("svd_finalize", st);
+                dim3 g(ceil_div(kout, 128), B);
+                k_unit_columns<T><<<g, 128, 0, st>>>(out + pO.off[s], out_stride, m, kout, w.nu, w.sSv);
+            }
             check();
+            {
+                THC_LAUNCH("svd_finalize", st);
+                THC_CUDA(launch_gemm<T>(B, kout, kout, n, RowMajorA<T>{w.V, w.sV, n}, TransB<T>{w.V, w.sV, n},
+                                        StoreRM<T>{w.F, w.sF, kout}, st));
+            }
+            {
+                THC_LAUNCH("svd_finalize", st);
+                THC_CUDA(launch_gemm<T>(B, kout, n, kout, CorrA<T>{w.F, w.sF, w.nu, w.sSv, kout},
+                                        RowMajorB<T>{w.V, w.sV, n}, StoreRM<T>{w.M[s & 1], w.sV, n}, st));
+            }
         }
         // ---- last site: M_{L-2} Q_{L-1}
         {

@@ -41,8 +41,9 @@ struct JacobiJob {
     double rot_tol;    // rotation threshold on |z_a.z_b| / (|z_a||z_b|)
     int max_sweeps;
     int* status;       // OR of DEV_* flags
-    double* dbg;       // [4]: p, n, rotations and max cosine of the last sweep of the
-                       // first matrix that did not converge (written once)
+    double* dbg;       // [8]: p, n, rotations and max cosine of the last sweep of the
+                       // first matrix that did not converge (written once); [4..7] as
+                       // counters: sweeps, matrices, sweeps and matrices with p >= 128
     int blk;           // row block of the blocked ordering (slot of 2*blk rows)
     const int* colmap; // optional per-term column permutation (n ints, stride n): Z's
                        // column c is column colmap[c] of C; V is written in C's order
@@ -53,80 +54,149 @@ __device__ __forceinline__ int rr_player(int pos, int r, int P2) {
     return pos == 0 ? 0 : ((pos - 1 + r) % (P2 - 1)) + 1;
 }
 
-// Rotate up to K independent pairs of rows at once (rows ra[i], rb[i], i < cnt)
-// so that every pair becomes orthogonal.  The K pairs are interleaved so their
-// loads, warp reductions and scalar chains overlap (instruction-level
-// parallelism hides the latencies that dominate one pair at a time).  The
-// rotation of each pair is decided and parametrised once (lane 0, in the
-// storage precision) and broadcast: every lane holds the same sums, and
-// float64 arithmetic is scarce on this part.  Returns the number of rotations.
+// Rotate up to K (1, 2 or 4) independent pairs of rows at once (rows ra[i],
+// rb[i], for the i set in the bit mask `valid`) so that every pair becomes
+// orthogonal.  The K pairs are
+// interleaved so their loads, reductions and scalar chains overlap.
+//   * Row layout per lane: with VEC = 16 / sizeof(T) and n a multiple of VEC
+//     (and 16-byte aligned rows), lane l owns the VEC-wide chunks starting at
+//     VEC*l + 32*VEC*q and moves them with 16-byte accesses; otherwise lane l
+//     owns columns l + 32*i.
+//   * The 3K sums (|a|^2, |b|^2, a.b per pair) are reduced by a reduce-scatter
+//     butterfly: each level hands half of the remaining values to the partner
+//     lane, so pair k's three sums end on the 32/K lanes with k = lane / (32/K).
+//   * Those lanes decide and parametrise pair k's rotation in the storage
+//     precision (float64 is scarce on this part) and the parameters are
+//     broadcast from the first lane of each group.
 template <class T, int NPL, int K>
-__device__ __forceinline__ int rotate_pairs(T* const (&ra)[K], T* const (&rb)[K], int cnt, int n,
+__device__ __forceinline__ int rotate_pairs(T* const (&ra)[K], T* const (&rb)[K], unsigned valid, int n,
                                             double rot_tol, double floor2, double& mycos) {
+    static_assert(K == 1 || K == 2 || K == 4, "pairs in flight");
+    constexpr int VEC = 16 / (int)sizeof(T);
     const int lane = threadIdx.x & 31;
+    const bool vec = (NPL % VEC == 0) && (n % VEC == 0);
     T xa[K][NPL], xb[K][NPL];
-    T sm[K][3];
+    // ---- loads
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        sm[k][0] = sm[k][1] = sm[k][2] = T(0);
+        if (vec) {
 #pragma unroll
-        for (int i = 0; i < NPL; ++i) {
-            const int c = lane + 32 * i;
-            const bool ok = k < cnt && c < n;
-            xa[k][i] = ok ? ra[k][c] : T(0);
-            xb[k][i] = ok ? rb[k][c] : T(0);
-        }
-    }
+            for (int q = 0; q < NPL / VEC; ++q) {
+                const int c = VEC * lane + 32 * VEC * q;
+                if (((valid >> k) & 1u) && c < n) {
+                    const uint4 va = *reinterpret_cast<const uint4*>(ra[k] + c);
+                    const uint4 vb = *reinterpret_cast<const uint4*>(rb[k] + c);
+                    const T* pa = reinterpret_cast<const T*>(&va);
+                    const T* pb = reinterpret_cast<const T*>(&vb);
 #pragma unroll
-    for (int k = 0; k < K; ++k)
+                    for (int e = 0; e < VEC; ++e) {
+                        xa[k][q * VEC + e] = pa[e];
+                        xb[k][q * VEC + e] = pb[e];
+                    }
+                } else {
 #pragma unroll
-        for (int i = 0; i < NPL; ++i) {
-            sm[k][0] += xa[k][i] * xa[k][i];
-            sm[k][1] += xb[k][i] * xb[k][i];
-            sm[k][2] += xa[k][i] * xb[k][i];
-        }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int k = 0; k < K; ++k)
-#pragma unroll
-            for (int j = 0; j < 3; ++j) sm[k][j] += __shfl_xor_sync(0xffffffffu, sm[k][j], o);
-    T cc[K], ss[K];
-    int rot = 0;  // bit k set: pair k rotates
-    if (lane == 0) {
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            cc[k] = T(1);
-            ss[k] = T(0);
-            const T al = sm[k][0], be = sm[k][1], ga = sm[k][2];
-            if (k < cnt && al > T(floor2) && be > T(floor2)) {
-                const T nab = sqrt(al) * sqrt(be);
-                const T ag = ga < T(0) ? -ga : ga;
-                mycos = fmax(mycos, (double)(ag / nab));
-                if (ag > T(rot_tol) * nab) {
-                    const T zeta = (be - al) / (T(2) * ga);
-                    const T az = zeta < T(0) ? -zeta : zeta;
-                    const T t = copysign(T(1), zeta) / (az + sqrt(T(1) + zeta * zeta));
-                    cc[k] = T(1) / sqrt(T(1) + t * t);
-                    ss[k] = cc[k] * t;
-                    rot |= 1 << k;
+                    for (int e = 0; e < VEC; ++e) xa[k][q * VEC + e] = xb[k][q * VEC + e] = T(0);
                 }
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < NPL; ++i) {
+                const int c = lane + 32 * i;
+                const bool ok = ((valid >> k) & 1u) && c < n;
+                xa[k][i] = ok ? ra[k][c] : T(0);
+                xb[k][i] = ok ? rb[k][c] : T(0);
             }
         }
     }
-    rot = __shfl_sync(0xffffffffu, rot, 0);
+    // ---- partial sums, value index v = 3k + {0: |a|^2, 1: |b|^2, 2: a.b}
+    T v[3 * K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        T s0 = 0, s1 = 0, s2 = 0;
+#pragma unroll
+        for (int i = 0; i < NPL; ++i) {
+            s0 += xa[k][i] * xa[k][i];
+            s1 += xb[k][i] * xb[k][i];
+            s2 += xa[k][i] * xb[k][i];
+        }
+        v[3 * k] = s0;
+        v[3 * k + 1] = s1;
+        v[3 * k + 2] = s2;
+    }
+    // ---- reduce-scatter over the pair index (all indices compile-time: the kept
+    // half moves to the front), then full butterflies on the last 3 values
+#pragma unroll
+    for (int lev = 0; (1 << lev) < K; ++lev) {
+        const int o = 16 >> lev;
+        const int half = (3 * K >> lev) / 2;
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < 3 * K / 2; ++i) {
+            if (i < half) {
+                const T send = upper ? v[i] : v[half + i];
+                const T keep = upper ? v[half + i] : v[i];
+                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
+        }
+    }
+    // this lane carries (|a|^2, |b|^2, a.b) of pair k = lane / (32/K)
+    T al = v[0], be = v[1], ga = v[2];
+#pragma unroll
+    for (int o = 32 / K / 2; o >= 1; o >>= 1) {
+        al += __shfl_xor_sync(0xffffffffu, al, o);
+        be += __shfl_xor_sync(0xffffffffu, be, o);
+        ga += __shfl_xor_sync(0xffffffffu, ga, o);
+    }
+    const int my_pair = lane / (32 / K);
+    T c = T(1), s = T(0);
+    bool rot = false;
+    if (((valid >> my_pair) & 1u) && al > T(floor2) && be > T(floor2)) {
+        const T nab = sqrt(al) * sqrt(be);
+        const T ag = ga < T(0) ? -ga : ga;
+        if ((lane & (32 / K - 1)) == 0) mycos = fmax(mycos, (double)(ag / nab));
+        if (ag > T(rot_tol) * nab) {
+            const T zeta = (be - al) / (T(2) * ga);
+            const T az = zeta < T(0) ? -zeta : zeta;
+            const T t = copysign(T(1), zeta) / (az + sqrt(T(1) + zeta * zeta));
+            c = T(1) / sqrt(T(1) + t * t);
+            s = c * t;
+            rot = true;
+        }
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, rot);
     int nrot = 0;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        if (!(rot >> k & 1)) continue;
-        const T c = __shfl_sync(0xffffffffu, cc[k], 0);
-        const T s = __shfl_sync(0xffffffffu, ss[k], 0);
+        const int src = k * (32 / K);
+        if (!((bal >> src) & 1u)) continue;
+        const T ck = __shfl_sync(0xffffffffu, c, src);
+        const T sk = __shfl_sync(0xffffffffu, s, src);
+        if (vec) {
 #pragma unroll
-        for (int i = 0; i < NPL; ++i) {
-            const int col = lane + 32 * i;
-            if (col < n) {
-                ra[k][col] = c * xa[k][i] - s * xb[k][i];
-                rb[k][col] = s * xa[k][i] + c * xb[k][i];
+            for (int q = 0; q < NPL / VEC; ++q) {
+                const int col = VEC * lane + 32 * VEC * q;
+                if (col < n) {
+                    uint4 va, vb;
+                    T* pa = reinterpret_cast<T*>(&va);
+                    T* pb = reinterpret_cast<T*>(&vb);
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) {
+                        const T x = xa[k][q * VEC + e], y = xb[k][q * VEC + e];
+                        pa[e] = ck * x - sk * y;
+                        pb[e] = sk * x + ck * y;
+                    }
+                    *reinterpret_cast<uint4*>(ra[k] + col) = va;
+                    *reinterpret_cast<uint4*>(rb[k] + col) = vb;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < NPL; ++i) {
+                const int col = lane + 32 * i;
+                if (col < n) {
+                    ra[k][col] = ck * xa[k][i] - sk * xb[k][i];
+                    rb[k][col] = sk * xa[k][i] + ck * xb[k][i];
+                }
             }
         }
         ++nrot;
@@ -139,8 +209,24 @@ __device__ __forceinline__ int rotate_pairs(T* const (&ra)[K], T* const (&rb)[K]
 template <class T, int NPL>
 struct PairsInFlight {
     static constexpr int raw = 128 / (NPL * (int)sizeof(T));
-    static constexpr int value = raw < 1 ? 1 : (raw > 4 ? 4 : raw);
+    static constexpr int value = raw >= 4 ? 4 : (raw >= 2 ? 2 : 1);
 };
+
+// CTA-wide copy of `count` elements; 16-byte vector accesses when both ends
+// are 16-byte aligned and the byte count is a multiple of 16.
+template <class T>
+__device__ __forceinline__ void cta_copy(T* dst, const T* src, long count) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (((reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src)) & 15) == 0 &&
+        (count * (long)sizeof(T)) % 16 == 0) {
+        const long nv = count * (long)sizeof(T) / 16;
+        uint4* d = reinterpret_cast<uint4*>(dst);
+        const uint4* s = reinterpret_cast<const uint4*>(src);
+        for (long i = tid; i < nv; i += nt) d[i] = s[i];
+    } else {
+        for (long i = tid; i < count; i += nt) dst[i] = src[i];
+    }
+}
 
 // Rows with ||z||^2 <= floor2 are numerically zero (below the rounding level of
 // the matrix they came from): they are not rotated, and the selection drops them.
@@ -158,26 +244,21 @@ __device__ int jacobi_sweep_smem(T* Z, int p, int n, int r0_unused, double rot_t
         for (int pi0 = wid * JK; pi0 < P2 / 2; pi0 += nw * JK) {
             T* ra[JK];
             T* rb[JK];
-            int cnt = 0;
+            unsigned valid = 0;
 #pragma unroll
             for (int k = 0; k < JK; ++k) {
                 const int pi = pi0 + k;
-                int a = -1, b = -1;
+                int a = p, b = p;
                 if (pi < P2 / 2) {
                     a = rr_player(pi, r, P2);
                     b = rr_player(P2 - 1 - pi, r, P2);
                 }
-                const bool ok = a >= 0 && a < p && b < p;
-                // valid pairs first so that cnt counts them
-                ra[k] = Z;
-                rb[k] = Z;
-                if (ok) {
-                    ra[cnt] = Z + (long)a * n;
-                    rb[cnt] = Z + (long)b * n;
-                    ++cnt;
-                }
+                const bool ok = a < p && b < p;
+                ra[k] = ok ? Z + (long)a * n : Z;
+                rb[k] = ok ? Z + (long)b * n : Z;
+                valid |= (ok ? 1u : 0u) << k;
             }
-            myrot += rotate_pairs<T, NPL, JK>(ra, rb, cnt, n, rot_tol, floor2, mycos);
+            myrot += rotate_pairs<T, NPL, JK>(ra, rb, valid, n, rot_tol, floor2, mycos);
         }
         __syncthreads();
     }
@@ -204,10 +285,10 @@ __device__ int jacobi_sweep_blocked(T* Z, int p, int n, int bs, T* slot, double 
     // intra-block pairs
     for (int kb = 0; kb < nbk; ++kb) {
         const int r0 = kb * bs, nr = min(bs, p - r0);
-        for (int i = tid; i < nr * n; i += nt) slot[i] = Z[(long)r0 * n + i];
+        cta_copy(slot, Z + (long)r0 * n, (long)nr * n);
         __syncthreads();
         myrot += jacobi_sweep_smem<T, NPL>(slot, nr, n, 0, rot_tol, floor2, mycos);
-        for (int i = tid; i < nr * n; i += nt) Z[(long)r0 * n + i] = slot[i];
+        cta_copy(Z + (long)r0 * n, slot, (long)nr * n);
         __syncthreads();
     }
     // cross-block pairs
@@ -219,31 +300,28 @@ __device__ int jacobi_sweep_blocked(T* Z, int p, int n, int bs, T* slot, double 
             const int rb0 = Bk * bs, nb = min(bs, p - rb0);
             T* sa = slot;
             T* sb = slot + (size_t)bs * n;
-            for (int i = tid; i < na * n; i += nt) sa[i] = Z[(long)ra0 * n + i];
-            for (int i = tid; i < nb * n; i += nt) sb[i] = Z[(long)rb0 * n + i];
+            cta_copy(sa, Z + (long)ra0 * n, (long)na * n);
+            cta_copy(sb, Z + (long)rb0 * n, (long)nb * n);
             __syncthreads();
             for (int sh = 0; sh < bs; ++sh) {
                 for (int i0 = wid * JK; i0 < bs; i0 += nw * JK) {
                     T* ra[JK];
                     T* rb[JK];
-                    int cnt = 0;
+                    unsigned valid = 0;
 #pragma unroll
                     for (int k = 0; k < JK; ++k) {
                         const int i = i0 + k, j = (i0 + k + sh) % bs;
-                        ra[k] = slot;
-                        rb[k] = slot;
-                        if (i < na && j < nb) {
-                            ra[cnt] = sa + (long)i * n;
-                            rb[cnt] = sb + (long)j * n;
-                            ++cnt;
-                        }
+                        const bool ok = i < na && j < nb;
+                        ra[k] = ok ? sa + (long)i * n : slot;
+                        rb[k] = ok ? sb + (long)j * n : slot;
+                        valid |= (ok ? 1u : 0u) << k;
                     }
-                    myrot += rotate_pairs<T, NPL, JK>(ra, rb, cnt, n, rot_tol, floor2, mycos);
+                    myrot += rotate_pairs<T, NPL, JK>(ra, rb, valid, n, rot_tol, floor2, mycos);
                 }
                 __syncthreads();
             }
-            for (int i = tid; i < na * n; i += nt) Z[(long)ra0 * n + i] = sa[i];
-            for (int i = tid; i < nb * n; i += nt) Z[(long)rb0 * n + i] = sb[i];
+            cta_copy(Z + (long)ra0 * n, sa, (long)na * n);
+            cta_copy(Z + (long)rb0 * n, sb, (long)nb * n);
             __syncthreads();
         }
     }
@@ -253,11 +331,11 @@ __device__ int jacobi_sweep_blocked(T* Z, int p, int n, int bs, T* slot, double 
 // Sweeps until a sweep applies no rotation (or the budget ends).  mode 1: Z in
 // shared memory; mode 0: Z in global memory with the blocked ordering.
 template <class T, int NPL>
-__device__ void jacobi_rows(T* Z, int p, int n, int in_smem, int bs, T* slot, double rot_tol, double floor2,
-                            int max_sweeps, int* nrot_sh, unsigned long long* maxcos_sh, int* status,
-                            double* dbg) {
+__device__ int jacobi_rows(T* Z, int p, int n, int in_smem, int bs, T* slot, double rot_tol, double floor2,
+                           int max_sweeps, int* nrot_sh, unsigned long long* maxcos_sh, int* status,
+                           double* dbg) {
     const int lane = threadIdx.x & 31;
-    if (p < 2) return;
+    if (p < 2) return 0;
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         if (threadIdx.x == 0) {
             *nrot_sh = 0;
@@ -273,7 +351,7 @@ __device__ void jacobi_rows(T* Z, int p, int n, int in_smem, int bs, T* slot, do
         const int total = *nrot_sh;
         const double mc = __longlong_as_double((long long)*maxcos_sh);
         __syncthreads();
-        if (total == 0) return;
+        if (total == 0) return sweep + 1;
         if (sweep == max_sweeps - 1 && threadIdx.x == 0) {
             atomicOr(status, DEV_NONCONVERGED);
             if (dbg && atomicCAS(reinterpret_cast<unsigned long long*>(dbg), 0ull,
@@ -284,6 +362,7 @@ __device__ void jacobi_rows(T* Z, int p, int n, int in_smem, int bs, T* slot, do
             }
         }
     }
+    return max_sweeps;
 }
 
 // One CTA per term.  Dynamic smem: Z (p*n*sizeof(T)) when it fits, plus
@@ -307,7 +386,7 @@ __global__ void __launch_bounds__(256) k_jacobi_select(JacobiJob<T> job, int z_i
     T* after = reinterpret_cast<T*>(smem_raw + ((p * (sizeof(double) + sizeof(int)) + 15) & ~15));
     if (z_in_smem) {
         Z = after;
-        for (int i = tid; i < p * n; i += nt) Z[i] = Zg[i];
+        cta_copy(Z, Zg, (long)p * n);
         __syncthreads();
     }
     // Frobenius norm (invariant under the rotations) sets the rounding floor
@@ -319,8 +398,17 @@ __global__ void __launch_bounds__(256) k_jacobi_select(JacobiJob<T> job, int z_i
     }
     const double fro2 = block_sum(part, red);
     const double floor2 = Real<T>::eps * Real<T>::eps * fro2;
-    jacobi_rows<T, NPL>(Z, p, n, z_in_smem, job.blk, after, job.rot_tol, floor2, job.max_sweeps, &nrot_sh,
-                        &maxcos_sh, job.status, job.dbg);
+    const int sweeps = jacobi_rows<T, NPL>(Z, p, n, z_in_smem, job.blk, after, job.rot_tol, floor2,
+                                           job.max_sweeps, &nrot_sh, &maxcos_sh, job.status, job.dbg);
+    if (tid == 0 && job.dbg) {  // sweep statistics: all matrices, and those with p >= 128
+        unsigned long long* st = reinterpret_cast<unsigned long long*>(job.dbg + 4);
+        atomicAdd(st + 0, (unsigned long long)sweeps);
+        atomicAdd(st + 1, 1ull);
+        if (p >= 128) {
+            atomicAdd(st + 2, (unsigned long long)sweeps);
+            atomicAdd(st + 3, 1ull);
+        }
+    }
     __syncthreads();
     // squared row norms in float64
     for (int r = wid; r < p; r += nw) {
@@ -386,50 +474,44 @@ __global__ void __launch_bounds__(256) k_jacobi_select(JacobiJob<T> job, int z_i
     }
 }
 
-// Finalisation per term: normalise the columns of U (mU x kout, row-major, in
-// place) and write M = N (I - F) V (kout x n) with F = V V^T - I on the rows
-// that are kept.  Dynamic smem: kout*kout T (F) + kout T (norms).
+// Finalisation per term, step 1: normalise the columns of U (mU x kout,
+// row-major, in place) and keep their norms nu (coalesced: thread j walks
+// column j).  Steps 2 and 3 are batched GEMMs on the engine side:
+// F = V V^T, then M = diag(nu) (I - F') V with F' = F - I on the kept rows.
 template <class T>
-__global__ void __launch_bounds__(256)
-k_svd_finalize(T* U, long strideU, int mU, const T* V, long strideV, int n, int kout,
-               T* M, long strideM) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* F = reinterpret_cast<T*>(smem_raw);
-    T* nu = F + (size_t)kout * kout;
-    const int b = blockIdx.x;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+__global__ void __launch_bounds__(256) k_unit_columns(T* U, long strideU, int mU, int kout, T* nu,
+                                                      long strideNu) {
+    const int b = blockIdx.y;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= kout) return;
     U += (long)b * strideU;
-    V += (long)b * strideV;
-    M += (long)b * strideM;
-    for (int j = wid; j < kout; j += nw) {
-        double acc = 0.0;
-        for (int r = lane; r < mU; r += 32) {
-            const double x = U[(long)r * kout + j];
-            acc += x * x;
-        }
-        acc = warp_sum(acc);
-        const double nrm = sqrt(acc);
-        const T inv = nrm > 0.0 ? T(1.0 / nrm) : T(0);
-        for (int r = lane; r < mU; r += 32) U[(long)r * kout + j] *= inv;
-        if (lane == 0) nu[j] = nrm > 0.0 ? T(nrm) : T(0);
+    double acc = 0.0;
+    for (int r = 0; r < mU; ++r) {
+        const double x = U[(long)r * kout + j];
+        acc += x * x;
     }
-    // F = V V^T - I (zero for rows that are zero)
-    for (int o = tid; o < kout * kout; o += nt) {
-        const int i = o / kout, j = o % kout;
-        T s = 0;
-        const T* vi = V + (long)i * n;
-        const T* vj = V + (long)j * n;
-        for (int c = 0; c < n; ++c) s += vi[c] * vj[c];
-        F[o] = (i == j) ? (s != T(0) ? s - T(1) : T(0)) : s;
-    }
-    __syncthreads();
-    for (int o = tid; o < kout * n; o += nt) {
-        const int i = o / n, c = o % n;
-        T s = V[(long)i * n + c];
-        for (int l = 0; l < kout; ++l) s -= F[i * kout + l] * V[(long)l * n + c];
-        M[o] = nu[i] * s;
-    }
+    const double nrm = sqrt(acc);
+    const T inv = nrm > 0.0 ? T(1.0 / nrm) : T(0);
+    for (int r = 0; r < mU; ++r) U[(long)r * kout + j] *= inv;
+    nu[(long)b * strideNu + j] = nrm > 0.0 ? T(nrm) : T(0);
 }
+
+// A-operand of M = diag(nu) (I - F') V: element (i, l) = nu_i (delta_il - F'_il),
+// F'_il = F_il - delta_il on kept (non-zero) rows, F' = 0 on dropped rows.
+template <class T>
+struct CorrA {
+    const T* F;
+    long sF;
+    const T* nu;
+    long sNu;
+    int k;
+    __device__ __forceinline__ T operator()(int b, int i, int l) const {
+        const T f = F[(long)b * sF + (long)i * k + l];
+        const T fii = F[(long)b * sF + (long)i * k + i];
+        if (fii == T(0)) return T(0);  // dropped row: M row stays zero
+        const T fp = (i == l) ? f - T(1) : f;
+        return nu[(long)b * sNu + i] * ((i == l ? T(1) : T(0)) - fp);
+    }
+};
 
 }  // namespace thc
