@@ -194,7 +194,7 @@ struct Engine {
                 job.colmap = nullptr;
                 {
                     THC_LAUNCH("qr_lq_sweep", st);
-                    k_qr<T><<<B, 256, qr_smem_bytes<T>(job.m, job.nb, job.tc), st>>>(job);
+                    k_qr<T><<<B, QR_THREADS, qr_smem_bytes<T>(job.m, job.nb, job.tc), st>>>(job);
                 }
                 check();
             }
@@ -237,7 +237,7 @@ struct Engine {
                 job.mode = QR_R_ROWS;
                 {
                     THC_LAUNCH("qr_svd_precond", st);
-                    k_qr<T><<<B, 256, qr_smem_bytes<T>(m, job.nb, job.tc), st>>>(job);
+                    k_qr<T><<<B, QR_THREADS, qr_smem_bytes<T>(m, job.nb, job.tc), st>>>(job);
                 }
                 check();
             } else {

@@ -51,7 +51,10 @@ struct JacobiJob {
 
 // player at tournament position `pos` in round r (position 0 fixed)
 __device__ __forceinline__ int rr_player(int pos, int r, int P2) {
-    return pos == 0 ? 0 : ((pos - 1 + r) % (P2 - 1)) + 1;
+    if (pos == 0) return 0;
+    int q = pos - 1 + r;  // < 2 (P2 - 1) since pos, r < P2
+    if (q >= P2 - 1) q -= P2 - 1;
+    return q + 1;
 }
 
 // Rotate up to K (1, 2 or 4) independent pairs of rows at once (rows ra[i],
@@ -70,7 +73,7 @@ __device__ __forceinline__ int rr_player(int pos, int r, int P2) {
 //     broadcast from the first lane of each group.
 template <class T, int NPL, int K>
 __device__ __forceinline__ int rotate_pairs(T* const (&ra)[K], T* const (&rb)[K], unsigned valid, int n,
-                                            double rot_tol, double floor2, double& mycos) {
+                                            T rot_tol, T floor2, T& mycos) {
     static_assert(K == 1 || K == 2 || K == 4, "pairs in flight");
     constexpr int VEC = 16 / (int)sizeof(T);
     const int lane = threadIdx.x & 31;
@@ -150,11 +153,12 @@ __device__ __forceinline__ int rotate_pairs(T* const (&ra)[K], T* const (&rb)[K]
     const int my_pair = lane / (32 / K);
     T c = T(1), s = T(0);
     bool rot = false;
-    if (((valid >> my_pair) & 1u) && al > T(floor2) && be > T(floor2)) {
+    if (((valid >> my_pair) & 1u) && al > floor2 && be > floor2) {
         const T nab = sqrt(al) * sqrt(be);
         const T ag = ga < T(0) ? -ga : ga;
-        if ((lane & (32 / K - 1)) == 0) mycos = fmax(mycos, (double)(ag / nab));
-        if (ag > T(rot_tol) * nab) {
+        const T cosv = ag / nab;
+        mycos = mycos > cosv ? mycos : cosv;
+        if (ag > rot_tol * nab) {
             const T zeta = (be - al) / (T(2) * ga);
             const T az = zeta < T(0) ? -zeta : zeta;
             const T t = copysign(T(1), zeta) / (az + sqrt(T(1) + zeta * zeta));
@@ -234,8 +238,7 @@ __device__ __forceinline__ void cta_copy(T* dst, const T* src, long count) {
 // Round-robin ordering over all p rows held in shared memory: p/2 disjoint
 // pairs per round, JK of them per warp at a time.
 template <class T, int NPL>
-__device__ int jacobi_sweep_smem(T* Z, int p, int n, int r0_unused, double rot_tol, double floor2,
-                                 double& mycos) {
+__device__ int jacobi_sweep_smem(T* Z, int p, int n, int r0_unused, T rot_tol, T floor2, T& mycos) {
     constexpr int JK = PairsInFlight<T, NPL>::value;
     const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int P2 = p + (p & 1);
@@ -274,8 +277,7 @@ __device__ int jacobi_sweep_smem(T* Z, int p, int n, int r0_unused, double rot_t
 // bs independent pairs per round, JK per warp.  Every pair of rows is rotated
 // exactly once per sweep, as in the cyclic method.
 template <class T, int NPL>
-__device__ int jacobi_sweep_blocked(T* Z, int p, int n, int bs, T* slot, double rot_tol, double floor2,
-                                    double& mycos) {
+__device__ int jacobi_sweep_blocked(T* Z, int p, int n, int bs, T* slot, T rot_tol, T floor2, T& mycos) {
     constexpr int JK = PairsInFlight<T, NPL>::value;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int wid = tid >> 5, nw = nt >> 5;
@@ -310,7 +312,9 @@ __device__ int jacobi_sweep_blocked(T* Z, int p, int n, int bs, T* slot, double 
                     unsigned valid = 0;
 #pragma unroll
                     for (int k = 0; k < JK; ++k) {
-                        const int i = i0 + k, j = (i0 + k + sh) % bs;
+                        const int i = i0 + k;
+                        int j = i + sh;  // (i + sh) mod bs, both < bs
+                        if (j >= bs) j -= bs;
                         const bool ok = i < na && j < nb;
                         ra[k] = ok ? sa + (long)i * n : slot;
                         rb[k] = ok ? sb + (long)j * n : slot;
@@ -342,11 +346,16 @@ __device__ int jacobi_rows(T* Z, int p, int n, int in_smem, int bs, T* slot, dou
             *maxcos_sh = 0ull;
         }
         __syncthreads();
-        double mycos = 0.0;
-        const int myrot = in_smem ? jacobi_sweep_smem<T, NPL>(Z, p, n, 0, rot_tol, floor2, mycos)
-                                  : jacobi_sweep_blocked<T, NPL>(Z, p, n, bs, slot, rot_tol, floor2, mycos);
+        T mycos = T(0);
+        const T rt = T(rot_tol), f2 = T(floor2);
+        const int myrot = in_smem ? jacobi_sweep_smem<T, NPL>(Z, p, n, 0, rt, f2, mycos)
+                                  : jacobi_sweep_blocked<T, NPL>(Z, p, n, bs, slot, rt, f2, mycos);
         if (lane == 0 && myrot) atomicAdd(nrot_sh, myrot);
-        if (lane == 0) atomicMax(maxcos_sh, (unsigned long long)__double_as_longlong(mycos));
+        {
+            double mc = (double)mycos;
+            for (int o = 16; o > 0; o >>= 1) mc = fmax(mc, __shfl_xor_sync(0xffffffffu, mc, o));
+            if (lane == 0) atomicMax(maxcos_sh, (unsigned long long)__double_as_longlong(mc));
+        }
         __syncthreads();
         const int total = *nrot_sh;
         const double mc = __longlong_as_double((long long)*maxcos_sh);

@@ -40,13 +40,15 @@ __host__ __device__ inline int qr_ldp(int m) { return m | 1; }  // odd stride: c
 
 #define QCOL(c) (cm ? cm[(c)] : (c))
 
+constexpr int QR_THREADS = 512;  // 16 warps: one CTA per SM hides latency with more warps
+
 __host__ __device__ inline int qr_gsize(int nb, int tc) { return nb * (tc > nb ? tc : nb); }
 
 template <class T>
 __host__ inline size_t qr_smem_bytes(int m, int nb, int tc) {
     return 64 * sizeof(double) + (size_t)(nb + tc) * qr_ldp(m) * sizeof(T) +
            (size_t)nb * nb * sizeof(T) + (size_t)qr_gsize(nb, tc) * sizeof(T) +
-           (size_t)8 * 32 * tc * sizeof(T);
+           (size_t)(QR_THREADS / 32) * 32 * tc * sizeof(T);
 }
 
 // Apply (H_p0 ... H_{p0+pw-1})^T (transpose=true, factorisation) or
@@ -54,11 +56,11 @@ __host__ inline size_t qr_smem_bytes(int m, int nb, int tc) {
 // of A, rows [p0, m).  P holds the panel's V (local rows, column i at
 // P + i*ldp, unit diagonal implicit), Tm its T matrix.  Tiles of TC columns go
 // through shared memory Y (column-major, stride ldp):
-//   G = V^T Y : lane i of every warp owns row i of G (TC accumulators), the 8
+//   G = V^T Y : lane i of every warp owns row i of G (TC accumulators), the
 //               warps split the rows of Y and their partial sums meet in Gp;
 //   G <- T^T G (or T G), all threads, one column entry each;
 //   Y -= V G  : each thread owns ROWS_PER_T rows of the tile and all TC columns.
-constexpr int QR_TC = 16;
+constexpr int QR_TC = 8;
 
 template <class T, int TC>
 __device__ void qr_block_apply(T* A, int ld, int m, int p0, int pw, int c_begin, int c_end,
@@ -133,7 +135,7 @@ __device__ void qr_block_apply(T* A, int ld, int m, int p0, int pw, int c_begin,
 }
 
 template <class T>
-__global__ void __launch_bounds__(256) k_qr(QRJob<T> job) {
+__global__ void __launch_bounds__(QR_THREADS) k_qr(QRJob<T> job) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int b = blockIdx.x;
     const int m = job.m, n = job.n, ld = job.ld, nb = job.nb, tc = job.tc;
@@ -216,18 +218,19 @@ __global__ void __launch_bounds__(256) k_qr(QRJob<T> job) {
             }
         }
         __syncthreads();
-        if (tid == 0) {
-            for (int j = 0; j < pw; ++j) {
-                const T tj = Tm[j * nb + j];
-                for (int i = 0; i < j; ++i) {
-                    T s = 0;
-                    for (int l = i; l < j; ++l) s += Tm[i * nb + l] * G[l * pw + j];
-                    Tm[i * nb + j] = -tj * s;
-                }
-                for (int i = j + 1; i < pw; ++i) Tm[i * nb + j] = 0;
+        // column j of T needs columns < j: one step per column, rows in parallel
+        for (int j = 0; j < pw; ++j) {
+            const T tj = Tm[j * nb + j];
+            if (tid < j) {
+                const int i = tid;
+                T s = 0;
+                for (int l = i; l < j; ++l) s += Tm[i * nb + l] * G[l * pw + j];
+                Tm[i * nb + j] = -tj * s;
+            } else if (tid > j && tid < pw) {
+                Tm[tid * nb + j] = 0;
             }
+            __syncthreads();
         }
-        __syncthreads();
         // keep T for forming Q; write the factored panel back
         for (int i = tid; i < nb * nb; i += nt) Tw[(p0 / nb) * nb * nb + i] = Tm[i];
         for (int i = tid; i < pw * R; i += nt) {
