@@ -37,16 +37,19 @@ L2_BYTES = 129 * 2 ** 20
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=2)
+    p.add_argument("--steps", type=int, default=1)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default=WORKLOAD)
-    p.add_argument("--fp64-terms", type=int, default=192, help="leading terms timed on the float64 path")
+    p.add_argument("--fp64-terms", type=int, default=96, help="leading terms timed on the float64 path")
     p.add_argument("--cpu-terms", type=int, default=12, help="terms in the oracle's CPU sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--batch", type=int, default=0)
+    p.add_argument("--terms", type=int, default=0,
+                   help="apply only the first TERMS terms per step (0 = all; for profiling slices)")
+    p.add_argument("--no-profile", action="store_true", help="skip the CUDA-event profiled step")
     return p.parse_args()
 
 
@@ -226,7 +229,12 @@ def run_ours(args):
     psi32 = [dev(a, torch.float32) for a in psi]
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
 
+    n_step = args.terms if args.terms > 0 else T
+
     def step():
+        if args.terms > 0:
+            return B.thc_apply_H(*H, psi32, D_max=D, path="fp32", batch=args.batch, term_begin=0,
+                                 term_end=args.terms)
         return B.thc_apply_H(*H, psi32, D_max=D, path="fp32", batch=args.batch)
 
     def barrier():
@@ -255,7 +263,7 @@ def run_ours(args):
         tt = torch.tensor([tot], device="cuda", dtype=torch.float64)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         tot = float(tt)
-    value = T * args.steps * world / tot
+    value = n_step * args.steps * world / tot
     ms_step = tot / args.steps * 1e3
 
     # ---- end to end through the public API with host buffers
@@ -266,28 +274,35 @@ def run_ours(args):
         h2d = sum(x.numel() * x.element_size() for x in hp + hH)
         d2h = 0
         tms = []
-        for _ in range(max(1, args.steps)):
+        for _ in range(1):  # one end-to-end step (each step is a full H|psi>)
             flush.fill_(1.0)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             dH = [x.to("cuda", non_blocking=True) for x in hH]
             dp = [x.to("cuda", non_blocking=True) for x in hp]
-            o = B.thc_apply_H(*dH, dp, D_max=D, path="fp32", batch=args.batch)
+            if args.terms > 0:
+                o = B.thc_apply_H(*dH, dp, D_max=D, path="fp32", batch=args.batch, term_begin=0,
+                                  term_end=args.terms)
+            else:
+                o = B.thc_apply_H(*dH, dp, D_max=D, path="fp32", batch=args.batch)
             res = [x.to("cpu", non_blocking=True) for x in o]
             e1.record()
             e1.synchronize()
             tms.append(e0.elapsed_time(e1))
             d2h = sum(x.numel() * x.element_size() for x in res)
-        e2e = {"value": T * len(tms) * world / (sum(tms) / 1e3), "unit": "terms/s",
+        e2e = {"value": n_step * len(tms) * world / (sum(tms) / 1e3), "unit": "terms/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     # ---- one profiled step: per-kernel CUDA-event durations for the roofline
-    B.profile_read()
-    B.profile_enable(True)
-    step()
-    torch.cuda.synchronize()
-    prof = B.profile_read()
-    B.profile_enable(False)
+    prof = {}
+    if not args.no_profile:
+        B.profile_read()
+        B.profile_enable(True)
+        step()
+        torch.cuda.synchronize()
+        prof = B.profile_read()
+        B.profile_enable(False)
+    stats = {k: prof.pop(k) for k in list(prof) if k.startswith("jacobi_s") or k.startswith("jacobi_b")}
 
     # ---- plain float64 per-term path on a leading subset of terms (extrapolated)
     fp64 = None
@@ -329,7 +344,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "L": w["L"], "N": w["N"], "D_max": D, "terms": T,
+        "config": {"workload": args.workload, "L": w["L"], "N": w["N"], "D_max": D, "terms": n_step,
                    "path": "fp32", "l2": "flushed between steps (256 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "hpsi_per_s": value / T,
@@ -340,6 +355,8 @@ def run_ours(args):
         "fp64": fp64,
         "speedup_vs_fp64": (value / world) / fp64["value"] if fp64 else None,
         "kernel_ms_per_step": {k: round(v["ms"], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])},
+        "jacobi_sweeps_per_svd": {k: round(v["ms"] / max(v["launches"], 1), 2) for k, v in stats.items()
+                                  if k.startswith("jacobi_sweeps")},
         "compressions_per_step": n_compress,
     }
     if not args.no_cpu_baseline and world == 1:

@@ -45,6 +45,12 @@ __device__ __forceinline__ A block_sum(A v, A* red) {
 
 __host__ __device__ __forceinline__ int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
+// square root and sign transfer in the storage precision (no silent promotion)
+__device__ __forceinline__ float tsqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double tsqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float tcopysign(float a, float b) { return copysignf(a, b); }
+__device__ __forceinline__ double tcopysign(double a, double b) { return copysign(a, b); }
+
 // Device-side status word bits (one int per launch group, read by the host).
 enum : int {
     DEV_OK = 0,

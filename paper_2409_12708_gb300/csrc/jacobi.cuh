@@ -154,15 +154,15 @@ __device__ __forceinline__ int rotate_pairs(T* const (&ra)[K], T* const (&rb)[K]
     T c = T(1), s = T(0);
     bool rot = false;
     if (((valid >> my_pair) & 1u) && al > floor2 && be > floor2) {
-        const T nab = sqrt(al) * sqrt(be);
+        const T nab = tsqrt(al) * tsqrt(be);
         const T ag = ga < T(0) ? -ga : ga;
         const T cosv = ag / nab;
         mycos = mycos > cosv ? mycos : cosv;
         if (ag > rot_tol * nab) {
             const T zeta = (be - al) / (T(2) * ga);
             const T az = zeta < T(0) ? -zeta : zeta;
-            const T t = copysign(T(1), zeta) / (az + sqrt(T(1) + zeta * zeta));
-            c = T(1) / sqrt(T(1) + t * t);
+            const T t = tcopysign(T(1), zeta) / (az + tsqrt(T(1) + zeta * zeta));
+            c = T(1) / tsqrt(T(1) + t * t);
             s = c * t;
             rot = true;
         }
