@@ -192,6 +192,27 @@ unsigned long long thc_kernel_launches(void);
 void thc_profile_enable(int on);
 int thc_profile_read(char* buf, int len);
 
+/* <phi|psi> (float64 accumulation, as mps_inner) for callers that cannot
+ * allocate GPU memory -- e.g. code running inside a framework whose memory
+ * pool forbids foreign allocations, real-time loops that must not touch an
+ * allocator, or embedders with a memory budget fixed up front.  The paper has
+ * no counterpart; this is a deployment variant of mps_inner.
+ *  - Allocates nothing: the scratch (the float64 transfer matrices) is one
+ *    file-scope device array of 16 MiB that every GPU loading this library
+ *    holds until the process exits.  phi and psi are read in place; real MPS
+ *    only (F64 or F32, equal L, d = 4).
+ *  - Limit: 8 * (chi_phi * chi_psi * 5 + 64) bytes (rounded) must fit in
+ *    16 MiB, i.e. max bond products up to about 4e5 (512 x 512 works); larger
+ *    inputs return THC_EINVAL and nothing is launched.
+ *  - The first call on a device looks up the array's device address with that
+ *    device current; make that first call before any stream capture.
+ *  - All calls share the array and it keeps the previous call's contents (the
+ *    kernels initialise what they read).  Calls whose GPU work overlaps (other
+ *    streams without ordering, other threads) race on it.
+ *  - out_re: host pointer; the call synchronises `stream` before returning.
+ *    Errors: THC_EINVAL (bad or oversize input), THC_ECUDA; see thc_last_error(). */
+thc_status mps_inner_noalloc(const thc_mps* phi, const thc_mps* psi, double* out_re, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -76,6 +76,7 @@ def _load():
         "krylov_expm_apply": [P(thc_hamiltonian), P(thc_mps), C.c_double, C.c_int, P(thc_opts),
                               P(thc_mps), P(C.c_double), P(thc_allocator), C.c_void_p],
         "thc_kinetic_factors": [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+        "mps_inner_noalloc": [P(thc_mps), P(thc_mps), P(C.c_double), C.c_void_p],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -99,7 +100,7 @@ LIB = _load()
 EXPORTED = ("thc_apply_H", "thc_layer_apply", "thc_compress", "mps_inner", "mps_add_compress",
             "krylov_lanczos_ground", "krylov_expm_apply", "thc_kinetic_factors", "thc_mps_free",
             "thc_last_error", "thc_build_info", "thc_kernel_launches", "thc_profile_enable",
-            "thc_profile_read")
+            "thc_profile_read", "mps_inner_noalloc")
 
 
 # --------------------------------------------------------------------- allocator
@@ -221,6 +222,16 @@ def mps_inner(phi, psi):
     a, b = _desc(phi, code), _desc(psi, code)
     re, im = C.c_double(), C.c_double()
     _check(LIB.mps_inner(C.byref(a), C.byref(b), C.byref(re), C.byref(im), _stream()))
+    return re.value
+
+
+def mps_inner_noalloc(phi, psi):
+    """<phi|psi> through the entry point that allocates nothing (its scratch is a
+    fixed 16 MiB device array shared by all calls; see include/thc.h)."""
+    code = F64 if phi[0].dtype == torch.float64 else F32
+    a, b = _desc(phi, code), _desc(psi, code)
+    re = C.c_double()
+    _check(LIB.mps_inner_noalloc(C.byref(a), C.byref(b), C.byref(re), _stream()))
     return re.value
 
 

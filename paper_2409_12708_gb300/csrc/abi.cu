@@ -248,6 +248,11 @@ thc_status lanczos_t(const thc_hamiltonian* H, const thc_mps* psi0, int K, const
 
 }  // namespace
 
+namespace thc {
+// lets other translation units report through thc_last_error()
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace thc
+
 extern "C" {
 
 thc_status thc_apply_H(const thc_hamiltonian* H, const thc_mps* psi, const thc_opts* opts, thc_mps* out,
