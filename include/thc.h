@@ -184,7 +184,8 @@ const char* thc_build_info(void);
  * since the last read into buf (NUL-terminated, truncated to len), resets the
  * sums, and returns the number of bytes the full text needs.  The entry
  * "jacobi_budget_exhausted" counts Jacobi SVDs that used their whole sweep
- * budget ("ms" then holds the largest remaining row cosine); with profiling on,
+ * budget ("ms" then holds the most rotations a last sweep still applied); with
+ * profiling on,
  * "jacobi_sweeps_all" / "jacobi_sweeps_p_ge_128" count the Jacobi SVDs
  * ("launches") and their sweeps ("ms" holds the sweep total).  Profiling adds
  * host work per launch; leave it off for timed runs. */

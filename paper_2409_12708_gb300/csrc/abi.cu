@@ -104,12 +104,13 @@ struct Call {
         if (f & thc::DEV_SMALL_NONCONV) return fail(THC_ETIMEOUT, "small eigensolver sweep budget exhausted");
         if (f & thc::DEV_NONCONVERGED) {
             // not an error: the projector correction keeps the state exact and the
-            // kept subspace is orthogonal to the last sweep's cosine; counted
+            // kept subspace is orthogonal to the rotation threshold of the last
+            // sweep; counted, with the rotations that sweep still applied
             auto& p = thc::profiler();
             std::lock_guard<std::mutex> g(p.mu);
             auto& x = p.acc["jacobi_budget_exhausted"];
             x.first += 1;
-            x.second = std::max(x.second, d[3]);
+            x.second = std::max(x.second, d[2]);
         }
         return THC_OK;
     }

@@ -39,6 +39,7 @@ struct Engine {
     int* dflag = nullptr;  // device status word
     double* ddbg = nullptr;  // device diagnostics of a non-converged Jacobi ([4])
     int sms = 152;
+    int smem_optin = 227 * 1024;  // largest dynamic shared memory a block may opt in to
 
     Engine(cudaStream_t s, const thc_allocator* a) : st(s) {
         al.a = a;
@@ -46,6 +47,7 @@ struct Engine {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         static bool attrs_done = false;
         if (!attrs_done) {
             set_attrs();
@@ -307,18 +309,17 @@ struct Engine {
         j.status = dflag;
         j.dbg = ddbg;
         j.colmap = colmap;
-        const size_t budget = 200 * 1024;
+        // rows of Z that fit in shared memory next to sigma^2 and the order
+        const size_t budget = (size_t)std::min(224 * 1024, smem_optin - 2048);
         const size_t base = ((size_t)p * (sizeof(double) + sizeof(int)) + 15) & ~(size_t)15;
-        const size_t zb = (size_t)p * n * sizeof(T);
-        const int in_smem = (base + zb <= budget) ? 1 : 0;
-        // blocked ordering: one shared-memory slot of 2*blk rows for the CTA
-        j.blk = (int)std::max<size_t>(1, std::min<size_t>(32, (budget - base) / (2 * (size_t)n * sizeof(T))));
-        const size_t smem = base + (in_smem ? zb : 2 * (size_t)j.blk * n * sizeof(T));
+        const size_t row = (size_t)n * sizeof(T);
+        j.ps = (int)std::min<size_t>((size_t)p, (budget - base) / row);
+        const size_t smem = base + (size_t)j.ps * row;
         THC_LAUNCH("jacobi_svd", st);
-        if (n <= 128) k_jacobi_select<T, 4><<<B, 256, smem, st>>>(j, in_smem);
-        else if (n <= 256) k_jacobi_select<T, 8><<<B, 256, smem, st>>>(j, in_smem);
-        else if (n <= 512) k_jacobi_select<T, 16><<<B, 256, smem, st>>>(j, in_smem);
-        else if (n <= 1024) k_jacobi_select<T, 32><<<B, 256, smem, st>>>(j, in_smem);
+        if (n <= 128) k_jacobi_select<T, 4><<<B, JacobiCfg<T, 4>::threads, smem, st>>>(j);
+        else if (n <= 256) k_jacobi_select<T, 8><<<B, JacobiCfg<T, 8>::threads, smem, st>>>(j);
+        else if (n <= 512) k_jacobi_select<T, 16><<<B, JacobiCfg<T, 16>::threads, smem, st>>>(j);
+        else if (n <= 1024) k_jacobi_select<T, 32><<<B, JacobiCfg<T, 32>::threads, smem, st>>>(j);
         else throw Error(THC_EUNSUPPORTED, "bond dimension above 512 is not supported");
         check();
     }

@@ -5,9 +5,11 @@
 // C when C is tall, Z = C otherwise).  One-sided Jacobi (Hestenes) rotates
 // pairs of rows of Z until all rows are mutually orthogonal; rotations are
 // orthogonal, so Z^T Z = C^T C is preserved and the rows end up as
-// sigma_j v_j^T with v_j the right singular vectors of C.  Rows are paired by
-// the round-robin (tournament) ordering, p/2 disjoint pairs per round, one warp
-// per pair with the two rows held in registers.
+// sigma_j v_j^T with v_j the right singular vectors of C.  Rows are visited in
+// a block ordering: blocks of R rows play a round-robin tournament, and one
+// warp holds the 2R rows of a block pair in registers while it rotates their
+// pairs, so shared-memory traffic is one read and write per R rotations of a
+// row.
 //
 // Selection (float64, the truncation decision): sigma_j^2 = ||z_j||^2 is
 // accumulated in double, rows are ranked by sigma, and the kept count follows
@@ -21,6 +23,8 @@
 // is reproduced to rounding error even though the Jacobi rows are orthogonal
 // only to the convergence threshold.
 #pragma once
+
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -41,10 +45,10 @@ struct JacobiJob {
     double rot_tol;    // rotation threshold on |z_a.z_b| / (|z_a||z_b|)
     int max_sweeps;
     int* status;       // OR of DEV_* flags
-    double* dbg;       // [8]: p, n, rotations and max cosine of the last sweep of the
-                       // first matrix that did not converge (written once); [4..7] as
+    double* dbg;       // [8]: p, n and the rotations of the last sweep of the first
+                       // matrix that did not converge (written once); [4..7] as
                        // counters: sweeps, matrices, sweeps and matrices with p >= 128
-    int blk;           // row block of the blocked ordering (slot of 2*blk rows)
+    int ps;            // rows of Z held in shared memory (the rest stay in global memory)
     const int* colmap; // optional per-term column permutation (n ints, stride n): Z's
                        // column c is column colmap[c] of C; V is written in C's order
 };
@@ -56,77 +60,148 @@ __device__ __forceinline__ int rr_player(int pos, int r, int P2) {
     if (q >= P2 - 1) q -= P2 - 1;
     return q + 1;
 }
+// ---------------------------------------------------------------------------
+// Row storage.  Rows [0, ps) of Z are copied to shared memory (Zs); rows
+// [ps, p) stay in global memory (Zg, L2-resident).  Both are reached through
+// generic pointers, so the sweep code is the same for either.
+template <class T>
+struct Rows {
+    T* Zs;
+    T* Zg;
+    int ps, n;
+    __device__ __forceinline__ T* operator()(int i) const { return i < ps ? Zs + (long)i * n : Zg + (long)i * n; }
+};
 
-// Rotate up to K (1, 2 or 4) independent pairs of rows at once (rows ra[i],
-// rb[i], for the i set in the bit mask `valid`) so that every pair becomes
-// orthogonal.  The K pairs are
-// interleaved so their loads, reductions and scalar chains overlap.
-//   * Row layout per lane: with VEC = 16 / sizeof(T) and n a multiple of VEC
-//     (and 16-byte aligned rows), lane l owns the VEC-wide chunks starting at
-//     VEC*l + 32*VEC*q and moves them with 16-byte accesses; otherwise lane l
-//     owns columns l + 32*i.
-//   * The 3K sums (|a|^2, |b|^2, a.b per pair) are reduced by a reduce-scatter
-//     butterfly: each level hands half of the remaining values to the partner
-//     lane, so pair k's three sums end on the 32/K lanes with k = lane / (32/K).
-//   * Those lanes decide and parametrise pair k's rotation in the storage
-//     precision (float64 is scarce on this part) and the parameters are
-//     broadcast from the first lane of each group.
-template <class T, int NPL, int K>
-__device__ __forceinline__ int rotate_pairs(T* const (&ra)[K], T* const (&rb)[K], unsigned valid, int n,
-                                            T rot_tol, T floor2, T& mycos) {
-    static_assert(K == 1 || K == 2 || K == 4, "pairs in flight");
+// compile-time loop: f(std::integral_constant<int, I>{}) for I in [B, E)
+template <int B, int E, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+    if constexpr (B < E) {
+        f(std::integral_constant<int, B>{});
+        static_for<B + 1, E>(f);
+    }
+}
+
+// Pair maps over the 2R rows one warp holds in registers: K = R disjoint pairs
+// at fixed register positions; the schedule moves rows between positions.
+template <int R>
+struct CrossPairs {  // (A_k, B_k): register rows k and R + k
+    static constexpr int K = R;
+    static constexpr int a(int k) { return k; }
+    static constexpr int b(int k) { return R + k; }
+};
+template <int R>
+struct CirclePairs {  // circle method over 2R positions: k with 2R - 1 - k
+    static constexpr int K = R;
+    static constexpr int a(int k) { return k; }
+    static constexpr int b(int k) { return 2 * R - 1 - k; }
+};
+
+// Launch shape per row length: R rows per block, so that the 2R rows of a
+// block pair (NPL values per lane each) take at most 64 registers per lane,
+// and 512 threads per CTA (256 where even R = 1 needs more registers).
+template <class T, int NPL>
+struct JacobiCfg {
+    static constexpr int regs_per_row = NPL * (int)sizeof(T) / 4;
+    static constexpr int raw = 32 / regs_per_row;
+    static constexpr int R = raw >= 8 ? 8 : (raw >= 4 ? 4 : (raw >= 2 ? 2 : 1));
+    static constexpr int threads = 2 * R * regs_per_row <= 64 ? 512 : 256;
+};
+
+// Row layout in registers: with VEC = 16 / sizeof(T), n a multiple of VEC and
+// 16-byte aligned rows (`vec`), lane l holds the VEC-wide chunks starting at
+// VEC*l + 32*VEC*q (16-byte accesses); otherwise columns l + 32*i.  Columns at
+// or beyond n are held as zeros.
+template <class T, int NPL>
+__device__ __forceinline__ void load_row(T (&x)[NPL], const T* row, bool ok, int n, bool vec) {
     constexpr int VEC = 16 / (int)sizeof(T);
     const int lane = threadIdx.x & 31;
-    const bool vec = (NPL % VEC == 0) && (n % VEC == 0);
-    T xa[K][NPL], xb[K][NPL];
-    // ---- loads
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
+    if constexpr (NPL % VEC == 0) {
         if (vec) {
 #pragma unroll
             for (int q = 0; q < NPL / VEC; ++q) {
                 const int c = VEC * lane + 32 * VEC * q;
-                if (((valid >> k) & 1u) && c < n) {
-                    const uint4 va = *reinterpret_cast<const uint4*>(ra[k] + c);
-                    const uint4 vb = *reinterpret_cast<const uint4*>(rb[k] + c);
-                    const T* pa = reinterpret_cast<const T*>(&va);
-                    const T* pb = reinterpret_cast<const T*>(&vb);
+                if (ok && c < n) {
+                    const uint4 u = *reinterpret_cast<const uint4*>(row + c);
+                    const T* pu = reinterpret_cast<const T*>(&u);
 #pragma unroll
-                    for (int e = 0; e < VEC; ++e) {
-                        xa[k][q * VEC + e] = pa[e];
-                        xb[k][q * VEC + e] = pb[e];
-                    }
+                    for (int e = 0; e < VEC; ++e) x[q * VEC + e] = pu[e];
                 } else {
 #pragma unroll
-                    for (int e = 0; e < VEC; ++e) xa[k][q * VEC + e] = xb[k][q * VEC + e] = T(0);
+                    for (int e = 0; e < VEC; ++e) x[q * VEC + e] = T(0);
                 }
             }
-        } else {
-#pragma unroll
-            for (int i = 0; i < NPL; ++i) {
-                const int c = lane + 32 * i;
-                const bool ok = ((valid >> k) & 1u) && c < n;
-                xa[k][i] = ok ? ra[k][c] : T(0);
-                xb[k][i] = ok ? rb[k][c] : T(0);
-            }
+            return;
         }
     }
-    // ---- partial sums, value index v = 3k + {0: |a|^2, 1: |b|^2, 2: a.b}
-    T v[3 * K];
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        T s0 = 0, s1 = 0, s2 = 0;
+    for (int i = 0; i < NPL; ++i) {
+        const int c = lane + 32 * i;
+        x[i] = (ok && c < n) ? row[c] : T(0);
+    }
+}
+
+template <class T, int NPL>
+__device__ __forceinline__ void store_row(const T (&x)[NPL], T* row, int n, bool vec) {
+    constexpr int VEC = 16 / (int)sizeof(T);
+    const int lane = threadIdx.x & 31;
+    if constexpr (NPL % VEC == 0) {
+        if (vec) {
+#pragma unroll
+            for (int q = 0; q < NPL / VEC; ++q) {
+                const int c = VEC * lane + 32 * VEC * q;
+                if (c < n) {
+                    uint4 u;
+                    T* pu = reinterpret_cast<T*>(&u);
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) pu[e] = x[q * VEC + e];
+                    *reinterpret_cast<uint4*>(row + c) = u;
+                }
+            }
+            return;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < NPL; ++i) {
+        const int c = lane + 32 * i;
+        if (c < n) row[c] = x[i];
+    }
+}
+
+// One step of K disjoint pair rotations on register-resident rows: every pair
+// (X[a], X[b]) of the map PM with both rows valid (bits of `vrows`) and both
+// norms above the floor is rotated so that the two rows become orthogonal.
+//   * The 3K sums (|a|^2, |b|^2, a.b per pair) are reduced by a reduce-scatter
+//     butterfly: each level hands half of the remaining values to the partner
+//     lane, so pair k's three sums end on the 32/K lanes with k = lane / (32/K).
+//   * Those lanes decide and parametrise pair k's rotation in the storage
+//     precision (float64 is scarce on this part); the parameters are
+//     broadcast from the first lane of each group.
+// The rotation is the classical one-sided Jacobi rotation (Hestenes): with
+// alpha = |a|^2, beta = |b|^2, gamma = a.b, zeta = (beta - alpha) / (2 gamma),
+// t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1 + t^2), s = c t.
+template <class T, int NPL, int NR, class PM>
+__device__ __forceinline__ int rotate_regs(T (&X)[NR][NPL], unsigned vrows, T rot_tol, T floor2) {
+    constexpr int K = PM::K;
+    static_assert(K == 1 || K == 2 || K == 4 || K == 8, "pairs per step");
+    const int lane = threadIdx.x & 31;
+    T v[3 * K];
+    unsigned pvalid = 0;
+    static_for<0, K>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        constexpr int a = PM::a(k), b = PM::b(k);
+        T s0 = T(0), s1 = T(0), s2 = T(0);
 #pragma unroll
         for (int i = 0; i < NPL; ++i) {
-            s0 += xa[k][i] * xa[k][i];
-            s1 += xb[k][i] * xb[k][i];
-            s2 += xa[k][i] * xb[k][i];
+            s0 += X[a][i] * X[a][i];
+            s1 += X[b][i] * X[b][i];
+            s2 += X[a][i] * X[b][i];
         }
         v[3 * k] = s0;
         v[3 * k + 1] = s1;
         v[3 * k + 2] = s2;
-    }
-    // ---- reduce-scatter over the pair index (all indices compile-time: the kept
+        pvalid |= ((vrows >> a) & (vrows >> b) & 1u) << k;
+    });
+    // reduce-scatter over the pair index (all indices compile-time: the kept
     // half moves to the front), then full butterflies on the last 3 values
 #pragma unroll
     for (int lev = 0; (1 << lev) < K; ++lev) {
@@ -142,7 +217,6 @@ __device__ __forceinline__ int rotate_pairs(T* const (&ra)[K], T* const (&rb)[K]
             }
         }
     }
-    // this lane carries (|a|^2, |b|^2, a.b) of pair k = lane / (32/K)
     T al = v[0], be = v[1], ga = v[2];
 #pragma unroll
     for (int o = 32 / K / 2; o >= 1; o >>= 1) {
@@ -153,11 +227,9 @@ __device__ __forceinline__ int rotate_pairs(T* const (&ra)[K], T* const (&rb)[K]
     const int my_pair = lane / (32 / K);
     T c = T(1), s = T(0);
     bool rot = false;
-    if (((valid >> my_pair) & 1u) && al > floor2 && be > floor2) {
+    if (((pvalid >> my_pair) & 1u) && al > floor2 && be > floor2) {
         const T nab = tsqrt(al) * tsqrt(be);
         const T ag = ga < T(0) ? -ga : ga;
-        const T cosv = ag / nab;
-        mycos = mycos > cosv ? mycos : cosv;
         if (ag > rot_tol * nab) {
             const T zeta = (be - al) / (T(2) * ga);
             const T az = zeta < T(0) ? -zeta : zeta;
@@ -169,52 +241,24 @@ __device__ __forceinline__ int rotate_pairs(T* const (&ra)[K], T* const (&rb)[K]
     }
     const unsigned bal = __ballot_sync(0xffffffffu, rot);
     int nrot = 0;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const int src = k * (32 / K);
-        if (!((bal >> src) & 1u)) continue;
-        const T ck = __shfl_sync(0xffffffffu, c, src);
-        const T sk = __shfl_sync(0xffffffffu, s, src);
-        if (vec) {
-#pragma unroll
-            for (int q = 0; q < NPL / VEC; ++q) {
-                const int col = VEC * lane + 32 * VEC * q;
-                if (col < n) {
-                    uint4 va, vb;
-                    T* pa = reinterpret_cast<T*>(&va);
-                    T* pb = reinterpret_cast<T*>(&vb);
-#pragma unroll
-                    for (int e = 0; e < VEC; ++e) {
-                        const T x = xa[k][q * VEC + e], y = xb[k][q * VEC + e];
-                        pa[e] = ck * x - sk * y;
-                        pb[e] = sk * x + ck * y;
-                    }
-                    *reinterpret_cast<uint4*>(ra[k] + col) = va;
-                    *reinterpret_cast<uint4*>(rb[k] + col) = vb;
-                }
-            }
-        } else {
+    static_for<0, K>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        constexpr int a = PM::a(k), b = PM::b(k);
+        constexpr int src = k * (32 / K);
+        if ((bal >> src) & 1u) {
+            const T ck = __shfl_sync(0xffffffffu, c, src);
+            const T sk = __shfl_sync(0xffffffffu, s, src);
 #pragma unroll
             for (int i = 0; i < NPL; ++i) {
-                const int col = lane + 32 * i;
-                if (col < n) {
-                    ra[k][col] = ck * xa[k][i] - sk * xb[k][i];
-                    rb[k][col] = sk * xa[k][i] + ck * xb[k][i];
-                }
+                const T x = X[a][i], y = X[b][i];
+                X[a][i] = ck * x - sk * y;
+                X[b][i] = sk * x + ck * y;
             }
+            ++nrot;
         }
-        ++nrot;
-    }
+    });
     return nrot;
 }
-
-// pairs per warp in flight: as many as keep the two rows of every pair within
-// 64 registers per lane (4 at most)
-template <class T, int NPL>
-struct PairsInFlight {
-    static constexpr int raw = 128 / (NPL * (int)sizeof(T));
-    static constexpr int value = raw >= 4 ? 4 : (raw >= 2 ? 2 : 1);
-};
 
 // CTA-wide copy of `count` elements; 16-byte vector accesses when both ends
 // are 16-byte aligned and the byte count is a multiple of 16.
@@ -232,133 +276,100 @@ __device__ __forceinline__ void cta_copy(T* dst, const T* src, long count) {
     }
 }
 
-// Rows with ||z||^2 <= floor2 are numerically zero (below the rounding level of
-// the matrix they came from): they are not rotated, and the selection drops them.
-//
-// Round-robin ordering over all p rows held in shared memory: p/2 disjoint
-// pairs per round, JK of them per warp at a time.
-template <class T, int NPL>
-__device__ int jacobi_sweep_smem(T* Z, int p, int n, int r0_unused, T rot_tol, T floor2, T& mycos) {
-    constexpr int JK = PairsInFlight<T, NPL>::value;
+// Move register rows [lo, hi] one position down, cyclically (row lo goes to
+// position hi), and their validity bits with them.
+template <class T, int NPL, int NR, int LO, int HI>
+__device__ __forceinline__ void cycle_rows(T (&X)[NR][NPL], unsigned& vrows) {
+    T tmp[NPL];
+#pragma unroll
+    for (int i = 0; i < NPL; ++i) tmp[i] = X[LO][i];
+#pragma unroll
+    for (int r = LO; r < HI; ++r)
+#pragma unroll
+        for (int i = 0; i < NPL; ++i) X[r][i] = X[r + 1][i];
+#pragma unroll
+    for (int i = 0; i < NPL; ++i) X[HI][i] = tmp[i];
+    constexpr unsigned span = (HI - LO + 1 == 32) ? 0xffffffffu : ((1u << (HI - LO + 1)) - 1u);
+    const unsigned seg = (vrows >> LO) & span;
+    const unsigned rot = (seg >> 1) | ((seg & 1u) << (HI - LO));
+    vrows = (vrows & ~(span << LO)) | (rot << LO);
+}
+
+// One sweep of the block ordering.  Rows are grouped in blocks of R; the
+// blocks play a round-robin tournament, and a warp takes the 2R rows of a
+// block pair (A, B) into registers once per visit:
+//   * in the first round (where every block plays once) it rotates all pairs
+//     of A u B by the circle method: position 0 stays, positions 1..2R-1 move
+//     cyclically after each of the 2R-1 steps of R pairs (k, 2R-1-k); this
+//     covers the pairs inside A and inside B;
+//   * in later rounds it rotates the R^2 cross pairs in R steps of the pairs
+//     (A_k, B_k), moving the B rows cyclically after each step.
+// After a visit every row is back at its position.  The step bodies are loops
+// over fixed register positions (not unrolled), so the code stays small.
+// Every pair of rows is rotated exactly once per sweep, as in the cyclic
+// method, while each row is read and written once per R rotations instead of
+// once per rotation.  Rows with ||z||^2 <= floor2 are numerically zero (below
+// the rounding level of the matrix they came from) and are not rotated.
+template <class T, int NPL, int R>
+__device__ int jacobi_sweep_reg(const Rows<T>& rows, int p, int n, bool vec, T rot_tol, T floor2) {
     const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int P2 = p + (p & 1);
-    int myrot = 0;
-    for (int r = 0; r < P2 - 1; ++r) {
-        for (int pi0 = wid * JK; pi0 < P2 / 2; pi0 += nw * JK) {
-            T* ra[JK];
-            T* rb[JK];
-            unsigned valid = 0;
-#pragma unroll
-            for (int k = 0; k < JK; ++k) {
-                const int pi = pi0 + k;
-                int a = p, b = p;
-                if (pi < P2 / 2) {
-                    a = rr_player(pi, r, P2);
-                    b = rr_player(P2 - 1 - pi, r, P2);
-                }
-                const bool ok = a < p && b < p;
-                ra[k] = ok ? Z + (long)a * n : Z;
-                rb[k] = ok ? Z + (long)b * n : Z;
-                valid |= (ok ? 1u : 0u) << k;
-            }
-            myrot += rotate_pairs<T, NPL, JK>(ra, rb, valid, n, rot_tol, floor2, mycos);
-        }
-        __syncthreads();
-    }
-    return myrot;
-}
-
-// Blocked ordering for Z too large for shared memory (Z stays in global
-// memory, L2-resident).  Rows are grouped in blocks of bs.  A sweep first
-// orthogonalises every block internally (round-robin inside the block), then
-// visits every pair of blocks once (round-robin over blocks); for a visited
-// pair (A, B) the CTA copies both blocks to shared memory and rotates the bs^2
-// cross pairs in bs shift rounds, round s pairing A_i with B_{(i+s) mod bs}:
-// bs independent pairs per round, JK per warp.  Every pair of rows is rotated
-// exactly once per sweep, as in the cyclic method.
-template <class T, int NPL>
-__device__ int jacobi_sweep_blocked(T* Z, int p, int n, int bs, T* slot, T rot_tol, T floor2, T& mycos) {
-    constexpr int JK = PairsInFlight<T, NPL>::value;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int wid = tid >> 5, nw = nt >> 5;
-    const int nbk = ceil_div(p, bs);
+    const int nbk = ceil_div(p, R);
     const int P2 = nbk + (nbk & 1);
+    constexpr unsigned lowR = (1u << R) - 1u;
     int myrot = 0;
-    // intra-block pairs
-    for (int kb = 0; kb < nbk; ++kb) {
-        const int r0 = kb * bs, nr = min(bs, p - r0);
-        cta_copy(slot, Z + (long)r0 * n, (long)nr * n);
-        __syncthreads();
-        myrot += jacobi_sweep_smem<T, NPL>(slot, nr, n, 0, rot_tol, floor2, mycos);
-        cta_copy(Z + (long)r0 * n, slot, (long)nr * n);
-        __syncthreads();
-    }
-    // cross-block pairs
     for (int rr = 0; rr < P2 - 1; ++rr) {
-        for (int bp = 0; bp < P2 / 2; ++bp) {
+        for (int bp = wid; bp < P2 / 2; bp += nw) {
             const int A = rr_player(bp, rr, P2), Bk = rr_player(P2 - 1 - bp, rr, P2);
-            if (A >= nbk || Bk >= nbk) continue;
-            const int ra0 = A * bs, na = min(bs, p - ra0);
-            const int rb0 = Bk * bs, nb = min(bs, p - rb0);
-            T* sa = slot;
-            T* sb = slot + (size_t)bs * n;
-            cta_copy(sa, Z + (long)ra0 * n, (long)na * n);
-            cta_copy(sb, Z + (long)rb0 * n, (long)nb * n);
-            __syncthreads();
-            for (int sh = 0; sh < bs; ++sh) {
-                for (int i0 = wid * JK; i0 < bs; i0 += nw * JK) {
-                    T* ra[JK];
-                    T* rb[JK];
-                    unsigned valid = 0;
+            T X[2 * R][NPL];
+            unsigned vrows = 0;
 #pragma unroll
-                    for (int k = 0; k < JK; ++k) {
-                        const int i = i0 + k;
-                        int j = i + sh;  // (i + sh) mod bs, both < bs
-                        if (j >= bs) j -= bs;
-                        const bool ok = i < na && j < nb;
-                        ra[k] = ok ? sa + (long)i * n : slot;
-                        rb[k] = ok ? sb + (long)j * n : slot;
-                        valid |= (ok ? 1u : 0u) << k;
-                    }
-                    myrot += rotate_pairs<T, NPL, JK>(ra, rb, valid, n, rot_tol, floor2, mycos);
-                }
-                __syncthreads();
+            for (int i = 0; i < 2 * R; ++i) {
+                const int blk = i < R ? A : Bk;
+                const int row = blk * R + (i < R ? i : i - R);
+                const bool ok = blk < nbk && row < p;
+                vrows |= (ok ? 1u : 0u) << i;
+                load_row<T, NPL>(X[i], ok ? rows(row) : rows.Zs, ok, n, vec);
             }
-            cta_copy(Z + (long)ra0 * n, sa, (long)na * n);
-            cta_copy(Z + (long)rb0 * n, sb, (long)nb * n);
-            __syncthreads();
+            if (rr == 0) {
+#pragma unroll 1
+                for (int st = 0; st < 2 * R - 1; ++st) {
+                    myrot += rotate_regs<T, NPL, 2 * R, CirclePairs<R>>(X, vrows, rot_tol, floor2);
+                    if constexpr (R > 1) cycle_rows<T, NPL, 2 * R, 1, 2 * R - 1>(X, vrows);
+                }
+            } else if ((vrows & lowR) && (vrows >> R)) {
+#pragma unroll 1
+                for (int st = 0; st < R; ++st) {
+                    myrot += rotate_regs<T, NPL, 2 * R, CrossPairs<R>>(X, vrows, rot_tol, floor2);
+                    if constexpr (R > 1) cycle_rows<T, NPL, 2 * R, R, 2 * R - 1>(X, vrows);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 2 * R; ++i) {
+                if ((vrows >> i) & 1u) {
+                    const int blk = i < R ? A : Bk;
+                    store_row<T, NPL>(X[i], rows(blk * R + (i < R ? i : i - R)), n, vec);
+                }
+            }
         }
+        __syncthreads();
     }
     return myrot;
 }
 
-// Sweeps until a sweep applies no rotation (or the budget ends).  mode 1: Z in
-// shared memory; mode 0: Z in global memory with the blocked ordering.
+// Sweeps until a sweep applies no rotation (or the budget ends).
 template <class T, int NPL>
-__device__ int jacobi_rows(T* Z, int p, int n, int in_smem, int bs, T* slot, double rot_tol, double floor2,
-                           int max_sweeps, int* nrot_sh, unsigned long long* maxcos_sh, int* status,
-                           double* dbg) {
+__device__ int jacobi_rows(const Rows<T>& rows, int p, int n, bool vec, double rot_tol, double floor2,
+                           int max_sweeps, int* nrot_sh, int* status, double* dbg) {
+    constexpr int R = JacobiCfg<T, NPL>::R;
     const int lane = threadIdx.x & 31;
     if (p < 2) return 0;
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-        if (threadIdx.x == 0) {
-            *nrot_sh = 0;
-            *maxcos_sh = 0ull;
-        }
+        if (threadIdx.x == 0) *nrot_sh = 0;
         __syncthreads();
-        T mycos = T(0);
-        const T rt = T(rot_tol), f2 = T(floor2);
-        const int myrot = in_smem ? jacobi_sweep_smem<T, NPL>(Z, p, n, 0, rt, f2, mycos)
-                                  : jacobi_sweep_blocked<T, NPL>(Z, p, n, bs, slot, rt, f2, mycos);
+        const int myrot = jacobi_sweep_reg<T, NPL, R>(rows, p, n, vec, T(rot_tol), T(floor2));
         if (lane == 0 && myrot) atomicAdd(nrot_sh, myrot);
-        {
-            double mc = (double)mycos;
-            for (int o = 16; o > 0; o >>= 1) mc = fmax(mc, __shfl_xor_sync(0xffffffffu, mc, o));
-            if (lane == 0) atomicMax(maxcos_sh, (unsigned long long)__double_as_longlong(mc));
-        }
         __syncthreads();
         const int total = *nrot_sh;
-        const double mc = __longlong_as_double((long long)*maxcos_sh);
         __syncthreads();
         if (total == 0) return sweep + 1;
         if (sweep == max_sweeps - 1 && threadIdx.x == 0) {
@@ -367,23 +378,20 @@ __device__ int jacobi_rows(T* Z, int p, int n, int in_smem, int bs, T* slot, dou
                                  (unsigned long long)__double_as_longlong((double)p)) == 0ull) {
                 dbg[1] = n;
                 dbg[2] = total;
-                dbg[3] = mc;
             }
         }
     }
     return max_sweeps;
 }
 
-// One CTA per term.  Dynamic smem: Z (p*n*sizeof(T)) when it fits, plus
-// p doubles (sigma^2) and p ints (order).
+// One CTA (JacobiCfg threads) per term.  Dynamic smem: p doubles (sigma^2), p ints
+// (order), then job.ps rows of Z.
 template <class T, int NPL>
-__global__ void __launch_bounds__(256) k_jacobi_select(JacobiJob<T> job, int z_in_smem) {
-    // z_in_smem: 1 = Z copied to shared memory; 0 = blocked ordering with Z in
-    // global memory and a shared-memory slot of 2*job.blk rows
+__global__ void __launch_bounds__(JacobiCfg<T, NPL>::threads) k_jacobi_select(JacobiJob<T> job) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int nrot_sh;
     __shared__ int kkeep_sh;
-    __shared__ unsigned long long maxcos_sh;
+    constexpr int VEC = 16 / (int)sizeof(T);
     const int b = blockIdx.x;
     const int p = job.p, n = job.n, kout = job.kout;
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -391,24 +399,26 @@ __global__ void __launch_bounds__(256) k_jacobi_select(JacobiJob<T> job, int z_i
     double* s2 = reinterpret_cast<double*>(smem_raw);
     int* order = reinterpret_cast<int*>(s2 + p);
     T* Zg = job.Z + (long)b * job.strideZ;
-    T* Z = Zg;
-    T* after = reinterpret_cast<T*>(smem_raw + ((p * (sizeof(double) + sizeof(int)) + 15) & ~15));
-    if (z_in_smem) {
-        Z = after;
-        cta_copy(Z, Zg, (long)p * n);
-        __syncthreads();
-    }
+    T* Zs = reinterpret_cast<T*>(smem_raw + ((p * (sizeof(double) + sizeof(int)) + 15) & ~15));
+    const int ps = min(job.ps, p);
+    cta_copy(Zs, Zg, (long)ps * n);
+    __syncthreads();
+    const Rows<T> rows{Zs, Zg, ps, n};
+    const bool vec = (n % VEC == 0) && ((reinterpret_cast<uintptr_t>(Zg) & 15) == 0);
     // Frobenius norm (invariant under the rotations) sets the rounding floor
     __shared__ double red[32];
     double part = 0.0;
-    for (int i = tid; i < p * n; i += nt) {
-        const double x = Z[i];
-        part += x * x;
+    for (int r = wid; r < p; r += nw) {
+        const T* z = rows(r);
+        for (int c = lane; c < n; c += 32) {
+            const double x = z[c];
+            part += x * x;
+        }
     }
     const double fro2 = block_sum(part, red);
     const double floor2 = Real<T>::eps * Real<T>::eps * fro2;
-    const int sweeps = jacobi_rows<T, NPL>(Z, p, n, z_in_smem, job.blk, after, job.rot_tol, floor2,
-                                           job.max_sweeps, &nrot_sh, &maxcos_sh, job.status, job.dbg);
+    const int sweeps = jacobi_rows<T, NPL>(rows, p, n, vec, job.rot_tol, floor2, job.max_sweeps, &nrot_sh,
+                                           job.status, job.dbg);
     if (tid == 0 && job.dbg) {  // sweep statistics: all matrices, and those with p >= 128
         unsigned long long* st = reinterpret_cast<unsigned long long*>(job.dbg + 4);
         atomicAdd(st + 0, (unsigned long long)sweeps);
@@ -421,24 +431,30 @@ __global__ void __launch_bounds__(256) k_jacobi_select(JacobiJob<T> job, int z_i
     __syncthreads();
     // squared row norms in float64
     for (int r = wid; r < p; r += nw) {
+        const T* z = rows(r);
         double acc = 0.0;
         for (int c = lane; c < n; c += 32) {
-            const double x = Z[(long)r * n + c];
+            const double x = z[c];
             acc += x * x;
         }
         acc = warp_sum(acc);
         if (lane == 0) s2[r] = acc;
     }
     __syncthreads();
-    // rank by descending sigma (ties by index): order[rank] = row
-    for (int r = tid; r < p; r += nt) {
-        const double v = s2[r];
-        int rank = 0;
-        for (int q = 0; q < p; ++q) {
-            const double w = s2[q];
-            rank += (w > v) || (w == v && q < r);
+    // rank by descending sigma (ties by index): order[rank] = row.  The squared
+    // norms are non-negative, so their bit patterns order like the values and
+    // the comparisons run on the integer pipe.
+    {
+        const long long* s2i = reinterpret_cast<const long long*>(s2);
+        for (int r = tid; r < p; r += nt) {
+            const long long v = s2i[r];
+            int rank = 0;
+            for (int q = 0; q < p; ++q) {
+                const long long w = s2i[q];
+                rank += (w > v) || (w == v && q < r);
+            }
+            order[rank] = r;
         }
-        order[rank] = r;
     }
     __syncthreads();
     if (tid == 0) {
@@ -477,9 +493,9 @@ __global__ void __launch_bounds__(256) k_jacobi_select(JacobiJob<T> job, int z_i
         }
         if (lane == 0) sv[j] = row >= 0 ? sig : 0.0;
         const double inv = row >= 0 ? 1.0 / sig : 0.0;
+        const T* z = row >= 0 ? rows(row) : nullptr;
         const int* cm = job.colmap ? job.colmap + (long)b * n : nullptr;
-        for (int c = lane; c < n; c += 32)
-            V[(long)j * n + (cm ? cm[c] : c)] = row >= 0 ? T(Z[(long)row * n + c] * inv) : T(0);
+        for (int c = lane; c < n; c += 32) V[(long)j * n + (cm ? cm[c] : c)] = z ? T(z[c] * inv) : T(0);
     }
 }
 
