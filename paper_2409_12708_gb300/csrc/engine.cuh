@@ -205,12 +205,11 @@ struct Plan {
 };
 
 template <class T>
-inline void qr_params(int m, int& nb, int& tc) {
+inline void qr_params(int m, int& nb) {
     nb = sizeof(T) == 8 ? 16 : 32;  // panel width (at most one warp of reflectors)
-    tc = QR_TC;                     // trailing tile width
     const size_t budget = 220 * 1024;
-    while (nb > 4 && qr_smem_bytes<T>(m, nb, tc) > budget) nb /= 2;
-    if (qr_smem_bytes<T>(m, nb, tc) > budget)
+    while (nb > 4 && qr_smem_bytes<T>(m, nb) > budget) nb /= 2;
+    if (qr_smem_bytes<T>(m, nb) > budget)
         throw Error(THC_EUNSUPPORTED, "QR column length too large for shared memory");
 }
 
@@ -241,8 +240,8 @@ inline Plan make_plan(int mode, const std::vector<int>& inA, const std::vector<i
         P.maxL = std::max(P.maxL, (long)P.e[s] * P.k[s]);
         const int m = 4 * P.k[s + 1], n = P.e[s];
         if (s >= 1) {
-            int nb, tc;
-            qr_params<T>(m, nb, tc);
+            int nb;
+            qr_params<T>(m, nb);
             P.maxTw = std::max(P.maxTw, (long)ceil_div(std::min(m, n), nb) * nb * nb);
             P.maxQRm = std::max<long>(P.maxQRm, m);
         }
@@ -257,8 +256,8 @@ inline Plan make_plan(int mode, const std::vector<int>& inA, const std::vector<i
         P.maxP = std::max(P.maxP, p);
         P.maxN = std::max(P.maxN, n);
         if (m > n) {
-            int nb, tc;
-            qr_params<T>(m, nb, tc);
+            int nb;
+            qr_params<T>(m, nb);
             P.maxTw = std::max(P.maxTw, (long)ceil_div(n, nb) * nb * nb);
             P.maxQRm = std::max<long>(P.maxQRm, m);
         }

@@ -191,12 +191,12 @@ struct Engine {
                 job.strideT = w.sTw;
                 job.out = w.Lb[s & 1];
                 job.strideOut = w.sL;
-                qr_params<T>(job.m, job.nb, job.tc);
+                qr_params<T>(job.m, job.nb);
                 job.mode = QR_L_AND_Q;
                 job.colmap = nullptr;
                 {
                     THC_LAUNCH("qr_lq_sweep", st);
-                    k_qr<T><<<B, QR_THREADS, qr_smem_bytes<T>(job.m, job.nb, job.tc), st>>>(job);
+                    k_qr<T><<<B, QR_THREADS, qr_smem_bytes<T>(job.m, job.nb), st>>>(job);
                 }
                 check();
             }
@@ -235,11 +235,11 @@ struct Engine {
                 job.strideT = w.sTw;
                 job.out = w.Z;
                 job.strideOut = w.sZ;
-                qr_params<T>(m, job.nb, job.tc);
+                qr_params<T>(m, job.nb);
                 job.mode = QR_R_ROWS;
                 {
                     THC_LAUNCH("qr_svd_precond", st);
-                    k_qr<T><<<B, QR_THREADS, qr_smem_bytes<T>(m, job.nb, job.tc), st>>>(job);
+                    k_qr<T><<<B, QR_THREADS, qr_smem_bytes<T>(m, job.nb), st>>>(job);
                 }
                 check();
             } else {

@@ -5,8 +5,10 @@
 // H_j = I - tau_j v_j v_j^T, v_j(j) = 1, v_j(i < j) = 0 (Golub & Van Loan,
 // Householder QR; the blocked form uses the compact WY representation
 // H_0 ... H_{b-1} = I - V T V^T of Schreiber & Van Loan).  Panels of nb columns
-// are factored in shared memory; the trailing columns are updated tile by tile
-// through shared memory, so the matrix is read and written once per panel.
+// are factored in shared memory; the trailing columns are updated in groups of
+// QR_QG columns straight from global memory with register-tiled products
+// (W = V^T Y, W <- T^T W, Y -= V W), so each group is read twice and written
+// once per panel.
 //
 // Modes (after the factorisation):
 //   QR_L_AND_Q : writes L = R^T (n x kk, row-major) and overwrites the first kk
@@ -30,107 +32,237 @@ struct QRJob {
     long strideT;
     T* out;        // L or R output
     long strideOut;
-    int nb, tc;    // panel width, trailing tile width
+    int nb;        // panel width
     int mode;
     const int* colmap;  // optional per-term column permutation (n ints, stride n):
                         // logical column c is stored in physical column colmap[c]
 };
 
-__host__ __device__ inline int qr_ldp(int m) { return m | 1; }  // odd stride: conflict-free
-
+// physical column of logical column c under the optional column map cm
 #define QCOL(c) (cm ? cm[(c)] : (c))
 
 constexpr int QR_THREADS = 512;  // 16 warps: one CTA per SM hides latency with more warps
+constexpr int QR_QG = 16;        // trailing columns per group
 
-__host__ __device__ inline int qr_gsize(int nb, int tc) { return nb * (tc > nb ? tc : nb); }
+// Column stride of the panel in shared memory: a multiple of 16 bytes (vector
+// access to 4 consecutive rows) that is 16 bytes past a multiple of 128, so
+// the columns a warp reads at once fall in distinct bank groups.
+template <class T>
+__host__ __device__ inline int qr_ldp(int m) {
+    return sizeof(T) == 4 ? (m + 31) / 32 * 32 + 4 : (m + 15) / 16 * 16 + 2;
+}
+
+// Reflector rows per lane in the register-tiled products (lane (ig, cg) owns
+// rows ig + 8 ii of W, ii < qr_ni(nb), and columns 4 cg .. 4 cg + 3).
+__host__ __device__ inline int qr_ni(int nb) { return nb >= 32 ? 4 : (nb >= 16 ? 2 : 1); }
 
 template <class T>
-__host__ inline size_t qr_smem_bytes(int m, int nb, int tc) {
-    return 64 * sizeof(double) + (size_t)(nb + tc) * qr_ldp(m) * sizeof(T) +
-           (size_t)nb * nb * sizeof(T) + (size_t)qr_gsize(nb, tc) * sizeof(T) +
-           (size_t)(QR_THREADS / 32) * 32 * tc * sizeof(T);
+__host__ inline size_t qr_smem_bytes(int m, int nb) {
+    const size_t cap = 8 * qr_ni(nb);  // rows of W per warp partial
+    return 64 * sizeof(double) + (size_t)nb * qr_ldp<T>(m) * sizeof(T) + 2 * (size_t)nb * nb * sizeof(T) +
+           ((size_t)(QR_THREADS / 32) * cap * QR_QG + 2 * cap * QR_QG) * sizeof(T);
+}
+
+// four consecutive elements with 16-byte accesses (p 16-byte aligned)
+template <class T>
+__device__ __forceinline__ void ld4(T (&x)[4], const T* p) {
+    if constexpr (sizeof(T) == 4) {
+        const float4 u = *reinterpret_cast<const float4*>(p);
+        x[0] = u.x;
+        x[1] = u.y;
+        x[2] = u.z;
+        x[3] = u.w;
+    } else {
+        const double2 a = *reinterpret_cast<const double2*>(p);
+        const double2 b = *reinterpret_cast<const double2*>(p + 2);
+        x[0] = a.x;
+        x[1] = a.y;
+        x[2] = b.x;
+        x[3] = b.y;
+    }
+}
+template <class T>
+__device__ __forceinline__ void st4(T* p, const T (&x)[4]) {
+    if constexpr (sizeof(T) == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
+    } else {
+        *reinterpret_cast<double2*>(p) = make_double2(x[0], x[1]);
+        *reinterpret_cast<double2*>(p + 2) = make_double2(x[2], x[3]);
+    }
+}
+// rows r .. r+3 of a global column (zeros at or beyond R); vector access when allowed
+template <class T>
+__device__ __forceinline__ void ld4_col(T (&x)[4], const T* col, int r, int R, bool vec) {
+    if (vec && r + 4 <= R) {
+        ld4(x, col + r);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) x[q] = r + q < R ? col[r + q] : T(0);
+    }
+}
+template <class T>
+__device__ __forceinline__ void st4_col(T* col, const T (&x)[4], int r, int R, bool vec) {
+    if (vec && r + 4 <= R) {
+        st4(col + r, x);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (r + q < R) col[r + q] = x[q];
+    }
 }
 
 // Apply (H_p0 ... H_{p0+pw-1})^T (transpose=true, factorisation) or
 // H_p0 ... H_{p0+pw-1} (transpose=false, forming Q) to columns [c_begin, c_end)
-// of A, rows [p0, m).  P holds the panel's V (local rows, column i at
-// P + i*ldp, unit diagonal implicit), Tm its T matrix.  Tiles of TC columns go
-// through shared memory Y (column-major, stride ldp):
-//   G = V^T Y : lane i of every warp owns row i of G (TC accumulators), the
-//               warps split the rows of Y and their partial sums meet in Gp;
-//   G <- T^T G (or T G), all threads, one column entry each;
-//   Y -= V G  : each thread owns ROWS_PER_T rows of the tile and all TC columns.
-constexpr int QR_TC = 8;
-
-template <class T, int TC>
-__device__ void qr_block_apply(T* A, int ld, int m, int p0, int pw, int c_begin, int c_end,
-                               const T* P, int ldp, const T* Tm, int nbT, T* Y, T* G, T* Gp,
-                               bool transpose, const int* cm) {
+// of A, rows [p0, m).  P holds the panel's V explicitly (column i at
+// P + i*ldp: zeros above row i, 1 at row i, zero rows from R up to the next
+// multiple of 4); Tm its T matrix.  Per group of QR_QG columns:
+//   W_w = V^T Y over the rows of warp w (lane (ig, cg): rows ig + 8 ii of W,
+//         columns 4 cg .. 4 cg + 3; four rows of Y per step), summed into W0;
+//   W1  = T^T W0 (or T W0);
+//   Y  -= V W1, each thread a tile of 4 rows x 4 columns.
+// Every product step is 16-byte loads and an outer-product of 4-vectors.
+template <class T, int NI>
+__device__ void qr_block_apply(T* A, int ld, int m, int p0, int pw, int c_begin, int c_end, const T* P, int ldp,
+                               const T* Tm, int nbT, T* Wp, T* W0, T* W1, bool transpose, const int* cm,
+                               bool vec) {
+    constexpr int CAP = 8 * NI;
     const int R = m - p0;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
-    for (int c0 = c_begin; c0 < c_end; c0 += TC) {
-        const int tcn = min(TC, c_end - c0);
-        for (int i = tid; i < TC * R; i += nt) {
-            const int c = i / R, r = i % R;
-            Y[c * ldp + r] = c < tcn ? A[(long)QCOL(c0 + c) * ld + p0 + r] : T(0);
-        }
-        __syncthreads();
-        // partial G over this warp's rows
+    const int ig = lane >> 2, cg = lane & 3;
+    const int R4 = ceil_div(R, 4);
+    const int qpw = ceil_div(R4, nw);
+    const int r0 = 4 * wid * qpw, r1 = min(R, 4 * (wid + 1) * qpw);
+    for (int c0 = c_begin; c0 < c_end; c0 += QR_QG) {
         {
-            T acc[TC];
+            T acc[NI][4];
 #pragma unroll
-            for (int c = 0; c < TC; ++c) acc[c] = T(0);
-            const int i = lane;
-            if (i < pw) {
-                const T* v = P + i * ldp;
-                const int rs = ceil_div(R, nw);
-                const int r0 = wid * rs, r1 = min(R, r0 + rs);
-                for (int r = max(r0, i); r < r1; ++r) {
-                    const T vr = (r == i) ? T(1) : v[r];
+            for (int ii = 0; ii < NI; ++ii)
 #pragma unroll
-                    for (int c = 0; c < TC; ++c) acc[c] += vr * Y[c * ldp + r];
+                for (int jj = 0; jj < 4; ++jj) acc[ii][jj] = T(0);
+            const T* yc[4];
+            bool cok[4];
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+                const int col = c0 + 4 * cg + jj;
+                cok[jj] = col < c_end;
+                yc[jj] = A + (long)QCOL(cok[jj] ? col : c0) * ld + p0;
+            }
+            for (int r = r0; r < r1; r += 4) {
+                T v[NI][4], y[4][4];
+#pragma unroll
+                for (int ii = 0; ii < NI; ++ii) {
+                    if (ig + 8 * ii < pw) {
+                        ld4(v[ii], P + (ig + 8 * ii) * ldp + r);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) v[ii][q] = T(0);
+                    }
                 }
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    if (cok[jj]) {
+                        ld4_col(y[jj], yc[jj], r, R, vec);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) y[jj][q] = T(0);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+#pragma unroll
+                    for (int ii = 0; ii < NI; ++ii)
+#pragma unroll
+                        for (int jj = 0; jj < 4; ++jj) acc[ii][jj] += v[ii][q] * y[jj][q];
             }
 #pragma unroll
-            for (int c = 0; c < TC; ++c) Gp[(wid * 32 + lane) * TC + c] = acc[c];
+            for (int ii = 0; ii < NI; ++ii)
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) Wp[(wid * CAP + ig + 8 * ii) * QR_QG + 4 * cg + jj] = acc[ii][jj];
         }
         __syncthreads();
-        for (int o = tid; o < pw * TC; o += nt) {
-            const int i = o / TC, c = o % TC;
+        for (int o = tid; o < pw * QR_QG; o += nt) {
             T s = 0;
-            for (int w = 0; w < nw; ++w) s += Gp[(w * 32 + i) * TC + c];
-            G[i * TC + c] = s;
+            for (int w = 0; w < nw; ++w) s += Wp[w * CAP * QR_QG + o];
+            W0[o] = s;
         }
         __syncthreads();
-        // G <- T^T G (factorisation) or T G (forming Q); T upper triangular
-        for (int o = tid; o < pw * TC; o += nt) {
-            const int i = o / TC, c = o % TC;
+        // W1 = T^T W0 (factorisation) or T W0 (forming Q); T upper triangular
+        for (int o = tid; o < pw * QR_QG; o += nt) {
+            const int i = o / QR_QG, c = o % QR_QG;
             T s = 0;
             if (transpose) {
-                for (int l = 0; l <= i; ++l) s += Tm[l * nbT + i] * G[l * TC + c];
+                for (int l = 0; l <= i; ++l) s += Tm[l * nbT + i] * W0[l * QR_QG + c];
             } else {
-                for (int l = i; l < pw; ++l) s += Tm[i * nbT + l] * G[l * TC + c];
+                for (int l = i; l < pw; ++l) s += Tm[i * nbT + l] * W0[l * QR_QG + c];
             }
-            Gp[i * TC + c] = s;
+            W1[o] = s;
         }
         __syncthreads();
-        // Y -= V G, written straight back to A
-        for (int r = tid; r < R; r += nt) {
-            T acc[TC];
+        // Y -= V W1 (consecutive threads take consecutive row quads of a column quad)
+        const int ncq = ceil_div(min(QR_QG, c_end - c0), 4);
+        for (int t = tid; t < R4 * ncq; t += nt) {
+            const int cq = t / R4, r = 4 * (t - cq * R4);
+            T* yc[4];
+            bool cok[4];
+            T y[4][4];
 #pragma unroll
-            for (int c = 0; c < TC; ++c) acc[c] = T(0);
-            const int top = min(r, pw - 1);
-            for (int l = 0; l <= top; ++l) {
-                const T v = (l == r) ? T(1) : P[l * ldp + r];
+            for (int jj = 0; jj < 4; ++jj) {
+                const int col = c0 + 4 * cq + jj;
+                cok[jj] = col < c_end;
+                yc[jj] = A + (long)QCOL(cok[jj] ? col : c0) * ld + p0;
+                if (cok[jj]) {
+                    ld4_col(y[jj], yc[jj], r, R, vec);
+                } else {
 #pragma unroll
-                for (int c = 0; c < TC; ++c) acc[c] += v * Gp[l * TC + c];
+                    for (int q = 0; q < 4; ++q) y[jj][q] = T(0);
+                }
+            }
+            T acc[4][4];
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[jj][q] = T(0);
+#pragma unroll 4
+            for (int i = 0; i < pw; ++i) {
+                T vq[4], w[4];
+                ld4(vq, P + i * ldp + r);
+                ld4(w, W1 + i * QR_QG + 4 * cq);
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[jj][q] += vq[q] * w[jj];
             }
 #pragma unroll
-            for (int c = 0; c < TC; ++c)
-                if (c < tcn) A[(long)QCOL(c0 + c) * ld + p0 + r] = Y[c * ldp + r] - acc[c];
+            for (int jj = 0; jj < 4; ++jj) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) y[jj][q] -= acc[jj][q];
+                if (cok[jj]) st4_col(yc[jj], y[jj], r, R, vec);
+            }
         }
         __syncthreads();
+    }
+}
+
+template <class T>
+__device__ __forceinline__ void qr_block_apply_nb(T* A, int ld, int m, int p0, int pw, int c_begin, int c_end,
+                                                  const T* P, int ldp, const T* Tm, int nbT, T* Wp, T* W0, T* W1,
+                                                  bool transpose, const int* cm, bool vec) {
+    const int ni = qr_ni(nbT);
+    if (ni == 4)
+        qr_block_apply<T, 4>(A, ld, m, p0, pw, c_begin, c_end, P, ldp, Tm, nbT, Wp, W0, W1, transpose, cm, vec);
+    else if (ni == 2)
+        qr_block_apply<T, 2>(A, ld, m, p0, pw, c_begin, c_end, P, ldp, Tm, nbT, Wp, W0, W1, transpose, cm, vec);
+    else
+        qr_block_apply<T, 1>(A, ld, m, p0, pw, c_begin, c_end, P, ldp, Tm, nbT, Wp, W0, W1, transpose, cm, vec);
+}
+
+// Panel in shared memory as explicit V: zeros above the diagonal, 1 on it.
+template <class T>
+__device__ __forceinline__ void qr_explicit_v(T* P, int ldp, int pw) {
+    for (int o = threadIdx.x; o < pw * pw; o += blockDim.x) {
+        const int i = o / pw, r = o % pw;  // column i, row r
+        if (r <= i) P[i * ldp + r] = (r == i) ? T(1) : T(0);
     }
 }
 
@@ -138,27 +270,32 @@ template <class T>
 __global__ void __launch_bounds__(QR_THREADS) k_qr(QRJob<T> job) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int b = blockIdx.x;
-    const int m = job.m, n = job.n, ld = job.ld, nb = job.nb, tc = job.tc;
+    const int m = job.m, n = job.n, ld = job.ld, nb = job.nb;
     const int kk = min(m, n);
-    const int ldp = qr_ldp(m);
+    const int ldp = qr_ldp<T>(m);
     T* A = job.A + (long)b * job.strideA;
     T* Tw = job.Tw + (long)b * job.strideT;
     const int* cm = job.colmap ? job.colmap + (long)b * n : nullptr;
-    double* red = reinterpret_cast<double*>(smem_raw);
-    T* P = reinterpret_cast<T*>(smem_raw + 64 * sizeof(double));
-    T* Y = P + (size_t)nb * ldp;
-    T* Tm = Y + (size_t)tc * ldp;
-    T* G = Tm + nb * nb;
-    T* Gp = G + qr_gsize(nb, tc);
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+    const int cap = 8 * qr_ni(nb);
+    double* red = reinterpret_cast<double*>(smem_raw);
+    T* P = reinterpret_cast<T*>(smem_raw + 64 * sizeof(double));
+    T* Tm = P + (size_t)nb * ldp;
+    T* G = Tm + nb * nb;
+    T* Wp = G + nb * nb;
+    T* W0 = Wp + (size_t)nw * cap * QR_QG;
+    T* W1 = W0 + (size_t)cap * QR_QG;
+    // 16-byte accesses to columns of A (rows p0 + r, r a multiple of 4)
+    const bool vec = ((reinterpret_cast<uintptr_t>(A) & 15) == 0) && (ld % 4 == 0);
 
     for (int p0 = 0; p0 < kk; p0 += nb) {
         const int pw = min(nb, kk - p0);
         const int R = m - p0;
-        for (int i = tid; i < pw * R; i += nt) {
-            const int c = i / R, r = i % R;
-            P[c * ldp + r] = A[(long)QCOL(p0 + c) * ld + p0 + r];
+        const int R4 = 4 * ceil_div(R, 4);
+        for (int i = tid; i < pw * R4; i += nt) {
+            const int c = i / R4, r = i % R4;
+            P[c * ldp + r] = r < R ? A[(long)QCOL(p0 + c) * ld + p0 + r] : T(0);
         }
         __syncthreads();
         // --- unblocked factorisation of the panel in shared memory
@@ -239,7 +376,11 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr(QRJob<T> job) {
         }
         __syncthreads();
         // --- trailing update of columns p0+pw .. n-1
-        qr_block_apply<T, QR_TC>(A, ld, m, p0, pw, p0 + pw, n, P, ldp, Tm, nb, Y, G, Gp, true, cm);
+        if (p0 + pw < n) {
+            qr_explicit_v(P, ldp, pw);
+            __syncthreads();
+            qr_block_apply_nb<T>(A, ld, m, p0, pw, p0 + pw, n, P, ldp, Tm, nb, Wp, W0, W1, true, cm, vec);
+        }
     }
 
     // --- outputs
@@ -263,14 +404,17 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr(QRJob<T> job) {
         const int p0 = pi * nb;
         const int pw = min(nb, kk - p0);
         const int R = m - p0;
-        for (int i = tid; i < pw * R; i += nt) {
-            const int c = i / R, r = i % R;
-            P[c * ldp + r] = A[(long)QCOL(p0 + c) * ld + p0 + r];
+        const int R4 = 4 * ceil_div(R, 4);
+        for (int i = tid; i < pw * R4; i += nt) {
+            const int c = i / R4, r = i % R4;
+            P[c * ldp + r] = r < R ? A[(long)QCOL(p0 + c) * ld + p0 + r] : T(0);
         }
         for (int i = tid; i < nb * nb; i += nt) Tm[i] = Tw[pi * nb * nb + i];
         __syncthreads();
+        qr_explicit_v(P, ldp, pw);
+        __syncthreads();
         if (p0 + pw < kk)
-            qr_block_apply<T, QR_TC>(A, ld, m, p0, pw, p0 + pw, kk, P, ldp, Tm, nb, Y, G, Gp, false, cm);
+            qr_block_apply_nb<T>(A, ld, m, p0, pw, p0 + pw, kk, P, ldp, Tm, nb, Wp, W0, W1, false, cm, vec);
         // panel columns in place (unblocked, backwards)
         for (int j = pw - 1; j >= 0; --j) {
             const T tj = Tm[j * nb + j];
