@@ -302,7 +302,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         prof = B.profile_read()
         B.profile_enable(False)
-    stats = {k: prof.pop(k) for k in list(prof) if k.startswith("jacobi_s") or k.startswith("jacobi_b")}
+    stats = {k: prof.pop(k) for k in list(prof) if k.startswith("jacobi_sweeps") or k.startswith("jacobi_budget")}
 
     # ---- plain float64 per-term path on a leading subset of terms (extrapolated)
     fp64 = None

@@ -81,29 +81,45 @@ __device__ __forceinline__ void static_for(F&& f) {
     }
 }
 
-// Pair maps over the 2R rows one warp holds in registers: K = R disjoint pairs
-// at fixed register positions; the schedule moves rows between positions.
+// Pair maps over the 2R rows one warp holds in registers: K = R disjoint pairs.
 template <int R>
-struct CrossPairs {  // (A_k, B_k): register rows k and R + k
+struct CrossPairs {  // (A_k, B_k): register rows k and R + k (rows moved between steps)
     static constexpr int K = R;
     static constexpr int a(int k) { return k; }
     static constexpr int b(int k) { return R + k; }
 };
+template <int R, int S>
+struct CrossShift {  // step S of the cross pairs in place: A_k with B_{(k+S) mod R}
+    static constexpr int K = R;
+    static constexpr int a(int k) { return k; }
+    static constexpr int b(int k) { return R + (k + S) % R; }
+};
+// player at position pos of round r of the circle method over P2 players
+__host__ __device__ constexpr int circle_player(int pos, int r, int P2) {
+    return pos == 0 ? 0 : (pos - 1 + r) % (P2 - 1) + 1;
+}
+template <int R, int S>
+struct CircleShift {  // round S of the circle method over the 2R rows in place
+    static constexpr int K = R;
+    static constexpr int a(int k) { return circle_player(k, S, 2 * R); }
+    static constexpr int b(int k) { return circle_player(2 * R - 1 - k, S, 2 * R); }
+};
 template <int R>
-struct CirclePairs {  // circle method over 2R positions: k with 2R - 1 - k
+struct CirclePairs {  // circle method over 2R positions: k with 2R - 1 - k (rows moved)
     static constexpr int K = R;
     static constexpr int a(int k) { return k; }
     static constexpr int b(int k) { return 2 * R - 1 - k; }
 };
 
-// Launch shape per row length: R rows per block, so that the 2R rows of a
-// block pair (NPL values per lane each) take at most 64 registers per lane,
+// Launch shape per row length: R rows per block (at most 4, which keeps the
+// unrolled steps small), so that the 2R rows of a block pair (NPL values per
+// lane each) take at most 64 registers per lane,
 // and 512 threads per CTA (256 where even R = 1 needs more registers).
 template <class T, int NPL>
 struct JacobiCfg {
     static constexpr int regs_per_row = NPL * (int)sizeof(T) / 4;
     static constexpr int raw = 32 / regs_per_row;
-    static constexpr int R = raw >= 8 ? 8 : (raw >= 4 ? 4 : (raw >= 2 ? 2 : 1));
+    static constexpr int R = raw >= 4 ? 4 : (raw >= 2 ? 2 : 1);
     static constexpr int threads = 2 * R * regs_per_row <= 64 ? 512 : 256;
 };
 
@@ -167,49 +183,58 @@ __device__ __forceinline__ void store_row(const T (&x)[NPL], T* row, int n, bool
     }
 }
 
+// Reciprocal, quotient and reciprocal square root for the rotation
+// parameters: the fast hardware approximations in float32 (arguments are kept
+// in range by the power-of-two scaling of the matrix), the library functions
+// in float64.
+__device__ __forceinline__ float fast_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fast_div(double a, double b) { return a / b; }
+__device__ __forceinline__ float fast_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double fast_rsqrt(double x) { return rsqrt(x); }
+
 // One step of K disjoint pair rotations on register-resident rows: every pair
 // (X[a], X[b]) of the map PM with both rows valid (bits of `vrows`) and both
 // norms above the floor is rotated so that the two rows become orthogonal.
-//   * The 3K sums (|a|^2, |b|^2, a.b per pair) are reduced by a reduce-scatter
-//     butterfly: each level hands half of the remaining values to the partner
-//     lane, so pair k's three sums end on the 32/K lanes with k = lane / (32/K).
+//   * nrm holds the squared norms of the 2R rows (the same in every lane): they
+//     are computed exactly when a visit loads its rows and then updated with
+//     the rotation identities |a'|^2 = |a|^2 - t (a.b), |b'|^2 = |b|^2 + t (a.b).
+//   * The K dot products a.b are reduced by a reduce-scatter butterfly: each
+//     level hands half of the remaining values to the partner lane, so pair
+//     k's dot ends on the 32/K lanes with k = lane / (32/K).
 //   * Those lanes decide and parametrise pair k's rotation in the storage
-//     precision (float64 is scarce on this part); the parameters are
+//     precision (float64 is scarce on this part); c, s and t (a.b) are
 //     broadcast from the first lane of each group.
 // The rotation is the classical one-sided Jacobi rotation (Hestenes): with
 // alpha = |a|^2, beta = |b|^2, gamma = a.b, zeta = (beta - alpha) / (2 gamma),
 // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1 + t^2), s = c t.
+// A pair is rotated when gamma^2 > rot_tol^2 alpha beta.  t may carry a few
+// units of rounding; c gets one Newton step, so that c^2 + s^2 = 1 holds to
+// rounding and the rotation stays orthogonal.
 template <class T, int NPL, int NR, class PM>
-__device__ __forceinline__ int rotate_regs(T (&X)[NR][NPL], unsigned vrows, T rot_tol, T floor2) {
+__device__ __forceinline__ int rotate_regs(T (&X)[NR][NPL], T (&nrm)[NR], unsigned vrows, T rt2, T floor2) {
     constexpr int K = PM::K;
     static_assert(K == 1 || K == 2 || K == 4 || K == 8, "pairs per step");
     const int lane = threadIdx.x & 31;
-    T v[3 * K];
+    T v[K];
     unsigned pvalid = 0;
     static_for<0, K>([&](auto kc) {
         constexpr int k = decltype(kc)::value;
         constexpr int a = PM::a(k), b = PM::b(k);
-        T s0 = T(0), s1 = T(0), s2 = T(0);
+        T g = T(0);
 #pragma unroll
-        for (int i = 0; i < NPL; ++i) {
-            s0 += X[a][i] * X[a][i];
-            s1 += X[b][i] * X[b][i];
-            s2 += X[a][i] * X[b][i];
-        }
-        v[3 * k] = s0;
-        v[3 * k + 1] = s1;
-        v[3 * k + 2] = s2;
+        for (int i = 0; i < NPL; ++i) g += X[a][i] * X[b][i];
+        v[k] = g;
         pvalid |= ((vrows >> a) & (vrows >> b) & 1u) << k;
     });
-    // reduce-scatter over the pair index (all indices compile-time: the kept
-    // half moves to the front), then full butterflies on the last 3 values
+    // reduce-scatter over the pair index (compile-time indices: the kept half
+    // moves to the front), then a full butterfly on the last value
 #pragma unroll
     for (int lev = 0; (1 << lev) < K; ++lev) {
         const int o = 16 >> lev;
-        const int half = (3 * K >> lev) / 2;
+        const int half = (K >> lev) / 2;
         const bool upper = (lane & o) != 0;
 #pragma unroll
-        for (int i = 0; i < 3 * K / 2; ++i) {
+        for (int i = 0; i < K / 2; ++i) {
             if (i < half) {
                 const T send = upper ? v[i] : v[half + i];
                 const T keep = upper ? v[half + i] : v[i];
@@ -217,27 +242,33 @@ __device__ __forceinline__ int rotate_regs(T (&X)[NR][NPL], unsigned vrows, T ro
             }
         }
     }
-    T al = v[0], be = v[1], ga = v[2];
+    T ga = v[0];
 #pragma unroll
-    for (int o = 32 / K / 2; o >= 1; o >>= 1) {
-        al += __shfl_xor_sync(0xffffffffu, al, o);
-        be += __shfl_xor_sync(0xffffffffu, be, o);
-        ga += __shfl_xor_sync(0xffffffffu, ga, o);
-    }
+    for (int o = 32 / K / 2; o >= 1; o >>= 1) ga += __shfl_xor_sync(0xffffffffu, ga, o);
     const int my_pair = lane / (32 / K);
-    T c = T(1), s = T(0);
-    bool rot = false;
-    if (((pvalid >> my_pair) & 1u) && al > floor2 && be > floor2) {
-        const T nab = tsqrt(al) * tsqrt(be);
-        const T ag = ga < T(0) ? -ga : ga;
-        if (ag > rot_tol * nab) {
-            const T zeta = (be - al) / (T(2) * ga);
-            const T az = zeta < T(0) ? -zeta : zeta;
-            const T t = tcopysign(T(1), zeta) / (az + tsqrt(T(1) + zeta * zeta));
-            c = T(1) / tsqrt(T(1) + t * t);
-            s = c * t;
-            rot = true;
+    T al = T(0), be = T(0);
+    static_for<0, K>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        if (k == my_pair) {
+            al = nrm[PM::a(k)];
+            be = nrm[PM::b(k)];
         }
+    });
+    T c = T(1), s = T(0), tg = T(0);
+    bool rot = false;
+    if (((pvalid >> my_pair) & 1u) && al > floor2 && be > floor2 && ga * ga > rt2 * (al * be)) {
+        const T zeta = fast_div(be - al, T(2) * ga);
+        const T az = zeta < T(0) ? -zeta : zeta;
+        const T q = T(1) + zeta * zeta;
+        const T root = az < T(1e18) ? q * fast_rsqrt(q) : az;
+        const T t = fast_div(tcopysign(T(1), zeta), az + root);
+        const T u = T(1) + t * t;
+        T cc = fast_rsqrt(u);
+        cc = cc * (T(1.5) - T(0.5) * u * cc * cc);
+        c = cc;
+        s = cc * t;
+        tg = t * ga;
+        rot = true;
     }
     const unsigned bal = __ballot_sync(0xffffffffu, rot);
     int nrot = 0;
@@ -248,12 +279,15 @@ __device__ __forceinline__ int rotate_regs(T (&X)[NR][NPL], unsigned vrows, T ro
         if ((bal >> src) & 1u) {
             const T ck = __shfl_sync(0xffffffffu, c, src);
             const T sk = __shfl_sync(0xffffffffu, s, src);
+            const T tgk = __shfl_sync(0xffffffffu, tg, src);
 #pragma unroll
             for (int i = 0; i < NPL; ++i) {
                 const T x = X[a][i], y = X[b][i];
                 X[a][i] = ck * x - sk * y;
                 X[b][i] = sk * x + ck * y;
             }
+            nrm[a] -= tgk;
+            nrm[b] += tgk;
             ++nrot;
         }
     });
@@ -277,18 +311,22 @@ __device__ __forceinline__ void cta_copy(T* dst, const T* src, long count) {
 }
 
 // Move register rows [lo, hi] one position down, cyclically (row lo goes to
-// position hi), and their validity bits with them.
+// position hi), with their norms and validity bits.
 template <class T, int NPL, int NR, int LO, int HI>
-__device__ __forceinline__ void cycle_rows(T (&X)[NR][NPL], unsigned& vrows) {
+__device__ __forceinline__ void cycle_rows(T (&X)[NR][NPL], T (&nrm)[NR], unsigned& vrows) {
     T tmp[NPL];
 #pragma unroll
     for (int i = 0; i < NPL; ++i) tmp[i] = X[LO][i];
+    const T tn = nrm[LO];
 #pragma unroll
-    for (int r = LO; r < HI; ++r)
+    for (int r = LO; r < HI; ++r) {
 #pragma unroll
         for (int i = 0; i < NPL; ++i) X[r][i] = X[r + 1][i];
+        nrm[r] = nrm[r + 1];
+    }
 #pragma unroll
     for (int i = 0; i < NPL; ++i) X[HI][i] = tmp[i];
+    nrm[HI] = tn;
     constexpr unsigned span = (HI - LO + 1 == 32) ? 0xffffffffu : ((1u << (HI - LO + 1)) - 1u);
     const unsigned seg = (vrows >> LO) & span;
     const unsigned rot = (seg >> 1) | ((seg & 1u) << (HI - LO));
@@ -297,21 +335,22 @@ __device__ __forceinline__ void cycle_rows(T (&X)[NR][NPL], unsigned& vrows) {
 
 // One sweep of the block ordering.  Rows are grouped in blocks of R; the
 // blocks play a round-robin tournament, and a warp takes the 2R rows of a
-// block pair (A, B) into registers once per visit:
+// block pair (A, B) into registers once per visit, with their squared norms:
 //   * in the first round (where every block plays once) it rotates all pairs
-//     of A u B by the circle method: position 0 stays, positions 1..2R-1 move
-//     cyclically after each of the 2R-1 steps of R pairs (k, 2R-1-k); this
-//     covers the pairs inside A and inside B;
-//   * in later rounds it rotates the R^2 cross pairs in R steps of the pairs
-//     (A_k, B_k), moving the B rows cyclically after each step.
-// After a visit every row is back at its position.  The step bodies are loops
-// over fixed register positions (not unrolled), so the code stays small.
-// Every pair of rows is rotated exactly once per sweep, as in the cyclic
-// method, while each row is read and written once per R rotations instead of
-// once per rotation.  Rows with ||z||^2 <= floor2 are numerically zero (below
-// the rounding level of the matrix they came from) and are not rotated.
+//     of A u B by the circle method (2R-1 steps of R pairs; unrolled for
+//     R <= 4, otherwise a loop over the fixed pairs (k, 2R-1-k) that moves
+//     rows 1..2R-1 cyclically after each step); this covers the pairs inside
+//     A and inside B;
+//   * in later rounds it rotates the R^2 cross pairs in R steps, step S pairing
+//     A_k with B_{(k+S) mod R} (unrolled for R <= 4, otherwise a loop over the
+//     fixed pairs (A_k, B_k) that moves the B rows after each step).
+// After a visit every row is back at its position.  Every pair of rows is
+// rotated exactly once per sweep, as in the cyclic method, while each row is
+// read and written once per R rotations instead of once per rotation.  Rows
+// with ||z||^2 <= floor2 are numerically zero (below the rounding level of the
+// matrix they came from) and are not rotated.
 template <class T, int NPL, int R>
-__device__ int jacobi_sweep_reg(const Rows<T>& rows, int p, int n, bool vec, T rot_tol, T floor2) {
+__device__ int jacobi_sweep_reg(const Rows<T>& rows, int p, int n, bool vec, T rt2, T floor2) {
     const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int nbk = ceil_div(p, R);
     const int P2 = nbk + (nbk & 1);
@@ -321,6 +360,7 @@ __device__ int jacobi_sweep_reg(const Rows<T>& rows, int p, int n, bool vec, T r
         for (int bp = wid; bp < P2 / 2; bp += nw) {
             const int A = rr_player(bp, rr, P2), Bk = rr_player(P2 - 1 - bp, rr, P2);
             T X[2 * R][NPL];
+            T nrm[2 * R];
             unsigned vrows = 0;
 #pragma unroll
             for (int i = 0; i < 2 * R; ++i) {
@@ -329,18 +369,40 @@ __device__ int jacobi_sweep_reg(const Rows<T>& rows, int p, int n, bool vec, T r
                 const bool ok = blk < nbk && row < p;
                 vrows |= (ok ? 1u : 0u) << i;
                 load_row<T, NPL>(X[i], ok ? rows(row) : rows.Zs, ok, n, vec);
+                T s2 = T(0);
+#pragma unroll
+                for (int e = 0; e < NPL; ++e) s2 += X[i][e] * X[i][e];
+                nrm[i] = s2;
             }
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1)
+#pragma unroll
+                for (int i = 0; i < 2 * R; ++i) nrm[i] += __shfl_xor_sync(0xffffffffu, nrm[i], o);
             if (rr == 0) {
+                if constexpr (R <= 4) {
+                    static_for<0, 2 * R - 1>([&](auto sc) {
+                        myrot += rotate_regs<T, NPL, 2 * R, CircleShift<R, decltype(sc)::value>>(X, nrm, vrows,
+                                                                                                 rt2, floor2);
+                    });
+                } else {
 #pragma unroll 1
-                for (int st = 0; st < 2 * R - 1; ++st) {
-                    myrot += rotate_regs<T, NPL, 2 * R, CirclePairs<R>>(X, vrows, rot_tol, floor2);
-                    if constexpr (R > 1) cycle_rows<T, NPL, 2 * R, 1, 2 * R - 1>(X, vrows);
+                    for (int st = 0; st < 2 * R - 1; ++st) {
+                        myrot += rotate_regs<T, NPL, 2 * R, CirclePairs<R>>(X, nrm, vrows, rt2, floor2);
+                        cycle_rows<T, NPL, 2 * R, 1, 2 * R - 1>(X, nrm, vrows);
+                    }
                 }
             } else if ((vrows & lowR) && (vrows >> R)) {
+                if constexpr (R <= 4) {
+                    static_for<0, R>([&](auto sc) {
+                        myrot += rotate_regs<T, NPL, 2 * R, CrossShift<R, decltype(sc)::value>>(X, nrm, vrows, rt2,
+                                                                                                floor2);
+                    });
+                } else {
 #pragma unroll 1
-                for (int st = 0; st < R; ++st) {
-                    myrot += rotate_regs<T, NPL, 2 * R, CrossPairs<R>>(X, vrows, rot_tol, floor2);
-                    if constexpr (R > 1) cycle_rows<T, NPL, 2 * R, R, 2 * R - 1>(X, vrows);
+                    for (int st = 0; st < R; ++st) {
+                        myrot += rotate_regs<T, NPL, 2 * R, CrossPairs<R>>(X, nrm, vrows, rt2, floor2);
+                        cycle_rows<T, NPL, 2 * R, R, 2 * R - 1>(X, nrm, vrows);
+                    }
                 }
             }
 #pragma unroll
@@ -366,7 +428,7 @@ __device__ int jacobi_rows(const Rows<T>& rows, int p, int n, bool vec, double r
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         if (threadIdx.x == 0) *nrot_sh = 0;
         __syncthreads();
-        const int myrot = jacobi_sweep_reg<T, NPL, R>(rows, p, n, vec, T(rot_tol), T(floor2));
+        const int myrot = jacobi_sweep_reg<T, NPL, R>(rows, p, n, vec, T(rot_tol * rot_tol), T(floor2));
         if (lane == 0 && myrot) atomicAdd(nrot_sh, myrot);
         __syncthreads();
         const int total = *nrot_sh;
@@ -405,17 +467,31 @@ __global__ void __launch_bounds__(JacobiCfg<T, NPL>::threads) k_jacobi_select(Ja
     __syncthreads();
     const Rows<T> rows{Zs, Zg, ps, n};
     const bool vec = (n % VEC == 0) && ((reinterpret_cast<uintptr_t>(Zg) & 15) == 0);
-    // Frobenius norm (invariant under the rotations) sets the rounding floor
+    // Frobenius norm (invariant under the rotations): it sets the rounding floor
+    // and a power-of-two scale (exact) that brings it near 1, which keeps every
+    // rotation parameter clear of underflow and overflow
     __shared__ double red[32];
-    double part = 0.0;
+    T tpart = T(0);
     for (int r = wid; r < p; r += nw) {
         const T* z = rows(r);
-        for (int c = lane; c < n; c += 32) {
-            const double x = z[c];
-            part += x * x;
-        }
+        for (int c = lane; c < n; c += 32) tpart += z[c] * z[c];
     }
-    const double fro2 = block_sum(part, red);
+    const double fro2_in = block_sum((double)tpart, red);
+    double scale = 1.0;
+    if (fro2_in > 0.0 && fro2_in < 1e300) {
+        int ex = 0;
+        frexp(fro2_in, &ex);
+        scale = ldexp(1.0, -(ex / 2));
+    }
+    if (scale != 1.0) {
+        const T sc = T(scale);
+        for (int r = wid; r < p; r += nw) {
+            T* z = rows(r);
+            for (int c = lane; c < n; c += 32) z[c] *= sc;
+        }
+        __syncthreads();
+    }
+    const double fro2 = fro2_in * scale * scale;
     const double floor2 = Real<T>::eps * Real<T>::eps * fro2;
     const int sweeps = jacobi_rows<T, NPL>(rows, p, n, vec, job.rot_tol, floor2, job.max_sweeps, &nrot_sh,
                                            job.status, job.dbg);
@@ -429,16 +505,14 @@ __global__ void __launch_bounds__(JacobiCfg<T, NPL>::threads) k_jacobi_select(Ja
         }
     }
     __syncthreads();
-    // squared row norms in float64
+    // squared row norms: per-lane partials in the storage precision, summed in
+    // float64
     for (int r = wid; r < p; r += nw) {
         const T* z = rows(r);
-        double acc = 0.0;
-        for (int c = lane; c < n; c += 32) {
-            const double x = z[c];
-            acc += x * x;
-        }
-        acc = warp_sum(acc);
-        if (lane == 0) s2[r] = acc;
+        T acc = T(0);
+        for (int c = lane; c < n; c += 32) acc += z[c] * z[c];
+        const double a = warp_sum((double)acc);
+        if (lane == 0) s2[r] = a;
     }
     __syncthreads();
     // rank by descending sigma (ties by index): order[rank] = row.  The squared
@@ -491,11 +565,11 @@ __global__ void __launch_bounds__(JacobiCfg<T, NPL>::threads) k_jacobi_select(Ja
             sig = sqrt(s2[row]);
             if (!(sig > thresh)) row = -1;
         }
-        if (lane == 0) sv[j] = row >= 0 ? sig : 0.0;
-        const double inv = row >= 0 ? 1.0 / sig : 0.0;
+        if (lane == 0) sv[j] = row >= 0 ? sig / scale : 0.0;
+        const T inv = row >= 0 ? T(1.0 / sig) : T(0);
         const T* z = row >= 0 ? rows(row) : nullptr;
         const int* cm = job.colmap ? job.colmap + (long)b * n : nullptr;
-        for (int c = lane; c < n; c += 32) V[(long)j * n + (cm ? cm[c] : c)] = z ? T(z[c] * inv) : T(0);
+        for (int c = lane; c < n; c += 32) V[(long)j * n + (cm ? cm[c] : c)] = z ? z[c] * inv : T(0);
     }
 }
 
