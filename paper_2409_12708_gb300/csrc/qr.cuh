@@ -111,137 +111,371 @@ __device__ __forceinline__ void st4_col(T* col, const T (&x)[4], int r, int R, b
     }
 }
 
+// Squared norm with about twice the storage precision.  A Householder
+// reflector is orthogonal only if beta^2 = alpha^2 + ||x||^2 holds to working
+// precision, and a plain float32 sum over ~10^3 entries misses that by ~1e-6,
+// which then compounds through the sweeps.  float: float-float accumulation
+// (Knuth's TwoSum with the exact product error from an FMA), no float64
+// arithmetic on the hot path; double: a plain sum.
+template <class T>
+struct SqAcc;
+template <>
+struct SqAcc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double x) { s += x * x; }
+    __device__ __forceinline__ double warp_total() { return warp_sum(s); }
+};
+template <>
+struct SqAcc<float> {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float p = x * x, e = fmaf(x, x, -p);
+        const float s = hi + p, bp = s - hi;
+        lo += ((hi - (s - bp)) + (p - bp)) + e;
+        hi = s;
+    }
+    // butterfly of float-float pairs; every lane ends with the same total
+    __device__ __forceinline__ double warp_total() {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+            const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+            const float s = hi + h2, bp = s - hi;
+            lo = (lo + l2) + ((hi - (s - bp)) + (h2 - bp));
+            hi = s;
+        }
+        return (double)hi + (double)lo;
+    }
+};
+
+// Squared norm of y[r0 .. R) by one warp (every lane gets the total).  In
+// float32, squares of entries below ~1e-19 underflow or lose their precision
+// (residues of rank-deficient columns are of that size), which would make the
+// reflector inconsistent with its vector; such small totals are recomputed
+// from float64 squares.
+template <class T>
+__device__ __forceinline__ double col_norm2(const T* y, int r0, int R) {
+    const int lane = threadIdx.x & 31;
+    SqAcc<T> a;
+    for (int r = r0 + lane; r < R; r += 32) a.add(y[r]);
+    double t = a.warp_total();
+    if (sizeof(T) == 4 && t < 1e-30) {
+        double s = 0.0;
+        for (int r = r0 + lane; r < R; r += 32) s += (double)y[r] * (double)y[r];
+        t = warp_sum(s);
+    }
+    return t;
+}
+
+// Register-tiled pieces of the compact-WY update with the panel's V held
+// explicitly in shared memory (column i at P + i*ldp: zeros above row i, 1 at
+// row i, zero rows from R up to the next multiple of 4).
+//
+// (1) Per-warp partial products Wp[w] = V^T Y over the rows of warp w for the
+//     QR_QG columns whose bases col(c) returns (c < QR_QG; null: no column).
+//     Lane (ig, cg) owns rows ig + 8 ii of W and columns 4 cg .. 4 cg + 3; each
+//     step takes four rows of V and Y with 16-byte loads.
+template <class T, int NI, class ColF>
+__device__ __forceinline__ void qr_vty(const T* P, int ldp, int pw, int R, T* Wp, ColF col, bool vec) {
+    constexpr int CAP = 8 * NI;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int ig = lane >> 2, cg = lane & 3;
+    const int R4 = ceil_div(R, 4), qpw = ceil_div(R4, nw);
+    const int r0 = 4 * wid * qpw, r1 = min(R, 4 * (wid + 1) * qpw);
+    T acc[NI][4];
+#pragma unroll
+    for (int ii = 0; ii < NI; ++ii)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) acc[ii][jj] = T(0);
+    const T* yc[4];
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) yc[jj] = col(4 * cg + jj);
+    for (int r = r0; r < r1; r += 4) {
+        T v[NI][4], y[4][4];
+#pragma unroll
+        for (int ii = 0; ii < NI; ++ii) {
+            if (ig + 8 * ii < pw) {
+                ld4(v[ii], P + (ig + 8 * ii) * ldp + r);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v[ii][q] = T(0);
+            }
+        }
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+            if (yc[jj]) {
+                ld4_col(y[jj], yc[jj], r, R, vec);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) y[jj][q] = T(0);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int ii = 0; ii < NI; ++ii)
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) acc[ii][jj] += v[ii][q] * y[jj][q];
+    }
+#pragma unroll
+    for (int ii = 0; ii < NI; ++ii)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) Wp[(wid * CAP + ig + 8 * ii) * QR_QG + 4 * cg + jj] = acc[ii][jj];
+}
+
+// (2) W0 = sum of the warp partials (pw x QR_QG)
+template <class T>
+__device__ __forceinline__ void qr_sum_partials(const T* Wp, T* W0, int pw, int cap) {
+    const int nw = blockDim.x >> 5;
+    for (int o = threadIdx.x; o < pw * QR_QG; o += blockDim.x) {
+        T s = 0;
+        for (int w = 0; w < nw; ++w) s += Wp[w * cap * QR_QG + o];
+        W0[o] = s;
+    }
+}
+
+// (3) W1 = T^T W0 (factorisation) or T W0 (forming Q); T upper triangular
+template <class T>
+__device__ __forceinline__ void qr_t_times(const T* Tm, int nbT, const T* W0, T* W1, int pw, bool transpose) {
+    for (int o = threadIdx.x; o < pw * QR_QG; o += blockDim.x) {
+        const int i = o / QR_QG, c = o % QR_QG;
+        T s = 0;
+        if (transpose) {
+            for (int l = 0; l <= i; ++l) s += Tm[l * nbT + i] * W0[l * QR_QG + c];
+        } else {
+            for (int l = i; l < pw; ++l) s += Tm[i * nbT + l] * W0[l * QR_QG + c];
+        }
+        W1[o] = s;
+    }
+}
+
+// (4) Y -= V W1 for ncols (<= QR_QG) columns, each thread a tile of 4 rows x 4
+//     columns (consecutive threads: consecutive row quads of a column quad).
+//     col(c) gives the base of column c in global memory.  IDENT: Y starts as
+//     the identity columns (local row cb + c of column c is 1) instead of
+//     being loaded.
+template <class T, bool IDENT, class ColF>
+__device__ __forceinline__ void qr_sub_vw(const T* P, int ldp, int pw, int R, const T* W1, int ncols, int cb,
+                                          ColF col, bool vec) {
+    const int R4 = ceil_div(R, 4), ncq = ceil_div(ncols, 4);
+    for (int t = threadIdx.x; t < R4 * ncq; t += blockDim.x) {
+        const int cq = t / R4, r = 4 * (t - cq * R4);
+        T* yc[4];
+        T y[4][4];
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+            const int c = 4 * cq + jj;
+            yc[jj] = c < ncols ? col(c) : nullptr;
+            if (IDENT) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) y[jj][q] = (r + q == cb + c) ? T(1) : T(0);
+            } else if (yc[jj]) {
+                ld4_col(y[jj], yc[jj], r, R, vec);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) y[jj][q] = T(0);
+            }
+        }
+        T acc[4][4];
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[jj][q] = T(0);
+#pragma unroll 4
+        for (int i = 0; i < pw; ++i) {
+            T vq[4], w[4];
+            ld4(vq, P + i * ldp + r);
+            ld4(w, W1 + i * QR_QG + 4 * cq);
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[jj][q] += vq[q] * w[jj];
+        }
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) y[jj][q] -= acc[jj][q];
+            if (yc[jj]) st4_col(yc[jj], y[jj], r, R, vec);
+        }
+    }
+}
+
 // Apply (H_p0 ... H_{p0+pw-1})^T (transpose=true, factorisation) or
 // H_p0 ... H_{p0+pw-1} (transpose=false, forming Q) to columns [c_begin, c_end)
-// of A, rows [p0, m).  P holds the panel's V explicitly (column i at
-// P + i*ldp: zeros above row i, 1 at row i, zero rows from R up to the next
-// multiple of 4); Tm its T matrix.  Per group of QR_QG columns:
-//   W_w = V^T Y over the rows of warp w (lane (ig, cg): rows ig + 8 ii of W,
-//         columns 4 cg .. 4 cg + 3; four rows of Y per step), summed into W0;
-//   W1  = T^T W0 (or T W0);
-//   Y  -= V W1, each thread a tile of 4 rows x 4 columns.
-// Every product step is 16-byte loads and an outer-product of 4-vectors.
+// of A, rows [p0, m), in groups of QR_QG columns: W = V^T Y, W <- T^T W (or
+// T W), Y -= V W.  Every product step is 16-byte loads and an outer product
+// of 4-vectors.
 template <class T, int NI>
 __device__ void qr_block_apply(T* A, int ld, int m, int p0, int pw, int c_begin, int c_end, const T* P, int ldp,
                                const T* Tm, int nbT, T* Wp, T* W0, T* W1, bool transpose, const int* cm,
                                bool vec) {
-    constexpr int CAP = 8 * NI;
     const int R = m - p0;
+    for (int c0 = c_begin; c0 < c_end; c0 += QR_QG) {
+        auto col = [&](int c) -> T* {
+            const int cc = c0 + c;
+            return cc < c_end ? A + (long)QCOL(cc) * ld + p0 : nullptr;
+        };
+        qr_vty<T, NI>(P, ldp, pw, R, Wp, col, vec);
+        __syncthreads();
+        qr_sum_partials(Wp, W0, pw, 8 * NI);
+        __syncthreads();
+        qr_t_times(Tm, nbT, W0, W1, pw, transpose);
+        __syncthreads();
+        qr_sub_vw<T, false>(P, ldp, pw, R, W1, min(QR_QG, c_end - c0), 0, col, vec);
+        __syncthreads();
+    }
+}
+
+// Columns p0 .. p0+pw-1 of Q = H_0 ... H_{kk-1} [I; 0] once the later panels
+// are applied: rows p0.. of those columns are H_p0 ... H_{p0+pw-1} E with E the
+// identity columns, i.e. E - V (T V1^T) with V1 the top pw x pw block of V
+// (V^T E = V1^T); rows above p0 are zero.
+template <class T>
+__device__ void qr_form_panel(T* A, int ld, int m, int p0, int pw, const T* P, int ldp, const T* Tm, int nbT,
+                              T* W0, T* W1, const int* cm, bool vec) {
+    const int R = m - p0;
+    for (int cb = 0; cb < pw; cb += QR_QG) {
+        const int gc = min(QR_QG, pw - cb);
+        for (int o = threadIdx.x; o < pw * QR_QG; o += blockDim.x) {
+            const int i = o / QR_QG, c = o % QR_QG;
+            W0[o] = c < gc ? P[i * ldp + cb + c] : T(0);
+        }
+        __syncthreads();
+        qr_t_times(Tm, nbT, W0, W1, pw, false);
+        __syncthreads();
+        auto col = [&](int c) -> T* { return A + (long)QCOL(p0 + cb + c) * ld + p0; };
+        qr_sub_vw<T, true>(P, ldp, pw, R, W1, gc, cb, col, vec);
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < pw * p0; i += blockDim.x) {
+        const int c = i / p0, r = i % p0;
+        A[(long)QCOL(p0 + c) * ld + r] = T(0);
+    }
+    __syncthreads();
+}
+
+// Panel in shared memory as explicit V: zeros above the diagonal, 1 on it.
+template <class T>
+__device__ __forceinline__ void qr_explicit_v(T* P, int ldp, int pw) {
+    for (int o = threadIdx.x; o < pw * pw; o += blockDim.x) {
+        const int i = o / pw, r = o % pw;  // column i, row r
+        if (r <= i) P[i * ldp + r] = (r == i) ? T(1) : T(0);
+    }
+}
+
+// Unblocked Householder factorisation of the panel P (R rows, zero-padded)
+// with two barriers per column: thread 0 forms reflector j from alpha = P[j][j]
+// and the squared norm below it (computed by warp 0 while it updated the
+// column in the previous step); then every warp applies H_j to its panel
+// columns with the unscaled x (the scale 1/(alpha - beta) is folded into the
+// dot and the update), warp 0 also forms the next column's norm, and all
+// threads scale the previous column, which no longer is read.  tau_j goes to
+// Tm[j][j], beta_j to P[j][j].
+template <class T>
+__device__ void qr_panel(T* P, int ldp, int R, int pw, T* Tm, int nb, T* psc, double* red) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
-    const int ig = lane >> 2, cg = lane & 3;
-    const int R4 = ceil_div(R, 4);
-    const int qpw = ceil_div(R4, nw);
-    const int r0 = 4 * wid * qpw, r1 = min(R, 4 * (wid + 1) * qpw);
-    for (int c0 = c_begin; c0 < c_end; c0 += QR_QG) {
-        {
-            T acc[NI][4];
-#pragma unroll
-            for (int ii = 0; ii < NI; ++ii)
-#pragma unroll
-                for (int jj = 0; jj < 4; ++jj) acc[ii][jj] = T(0);
-            const T* yc[4];
-            bool cok[4];
-#pragma unroll
-            for (int jj = 0; jj < 4; ++jj) {
-                const int col = c0 + 4 * cg + jj;
-                cok[jj] = col < c_end;
-                yc[jj] = A + (long)QCOL(cok[jj] ? col : c0) * ld + p0;
-            }
-            for (int r = r0; r < r1; r += 4) {
-                T v[NI][4], y[4][4];
-#pragma unroll
-                for (int ii = 0; ii < NI; ++ii) {
-                    if (ig + 8 * ii < pw) {
-                        ld4(v[ii], P + (ig + 8 * ii) * ldp + r);
-                    } else {
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) v[ii][q] = T(0);
-                    }
-                }
-#pragma unroll
-                for (int jj = 0; jj < 4; ++jj) {
-                    if (cok[jj]) {
-                        ld4_col(y[jj], yc[jj], r, R, vec);
-                    } else {
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) y[jj][q] = T(0);
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-#pragma unroll
-                    for (int ii = 0; ii < NI; ++ii)
-#pragma unroll
-                        for (int jj = 0; jj < 4; ++jj) acc[ii][jj] += v[ii][q] * y[jj][q];
-            }
-#pragma unroll
-            for (int ii = 0; ii < NI; ++ii)
-#pragma unroll
-                for (int jj = 0; jj < 4; ++jj) Wp[(wid * CAP + ig + 8 * ii) * QR_QG + 4 * cg + jj] = acc[ii][jj];
-        }
-        __syncthreads();
-        for (int o = tid; o < pw * QR_QG; o += nt) {
-            T s = 0;
-            for (int w = 0; w < nw; ++w) s += Wp[w * CAP * QR_QG + o];
-            W0[o] = s;
-        }
-        __syncthreads();
-        // W1 = T^T W0 (factorisation) or T W0 (forming Q); T upper triangular
-        for (int o = tid; o < pw * QR_QG; o += nt) {
-            const int i = o / QR_QG, c = o % QR_QG;
-            T s = 0;
-            if (transpose) {
-                for (int l = 0; l <= i; ++l) s += Tm[l * nbT + i] * W0[l * QR_QG + c];
-            } else {
-                for (int l = i; l < pw; ++l) s += Tm[i * nbT + l] * W0[l * QR_QG + c];
-            }
-            W1[o] = s;
-        }
-        __syncthreads();
-        // Y -= V W1 (consecutive threads take consecutive row quads of a column quad)
-        const int ncq = ceil_div(min(QR_QG, c_end - c0), 4);
-        for (int t = tid; t < R4 * ncq; t += nt) {
-            const int cq = t / R4, r = 4 * (t - cq * R4);
-            T* yc[4];
-            bool cok[4];
-            T y[4][4];
-#pragma unroll
-            for (int jj = 0; jj < 4; ++jj) {
-                const int col = c0 + 4 * cq + jj;
-                cok[jj] = col < c_end;
-                yc[jj] = A + (long)QCOL(cok[jj] ? col : c0) * ld + p0;
-                if (cok[jj]) {
-                    ld4_col(y[jj], yc[jj], r, R, vec);
-                } else {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) y[jj][q] = T(0);
+    if (wid == 0) {
+        const double t = col_norm2(P, 1, R);
+        if (lane == 0) red[0] = t;
+    }
+    __syncthreads();
+    for (int j = 0; j < pw; ++j) {
+        T* x = P + j * ldp;
+        if (tid == 0) {
+            const double xn2 = red[j & 1];
+            const T alpha = x[j];
+            T tau = T(0), scale = T(0);
+            const double a2 = (double)alpha * (double)alpha + xn2;
+            // a sub-column below (1e-30)^2 (float32) is treated as zero
+            if (xn2 > 0.0 && a2 > (sizeof(T) == 4 ? 1e-60 : 0.0)) {
+                if (sizeof(T) == 4 && a2 >= 1e-36) {
+                    const T beta = -tcopysign(tsqrt(T(a2)), alpha);
+                    tau = (beta - alpha) / beta;
+                    scale = T(1) / (alpha - beta);
+                    x[j] = beta;
+                } else {  // float64 (and float32 columns too small for float32 arithmetic)
+                    const double al = alpha;
+                    const double beta = -copysign(sqrt(a2), al);
+                    tau = T((beta - al) / beta);
+                    scale = T(1.0 / (al - beta));
+                    x[j] = T(beta);
                 }
             }
-            T acc[4][4];
-#pragma unroll
-            for (int jj = 0; jj < 4; ++jj)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) acc[jj][q] = T(0);
-#pragma unroll 4
-            for (int i = 0; i < pw; ++i) {
-                T vq[4], w[4];
-                ld4(vq, P + i * ldp + r);
-                ld4(w, W1 + i * QR_QG + 4 * cq);
-#pragma unroll
-                for (int jj = 0; jj < 4; ++jj)
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) acc[jj][q] += vq[q] * w[jj];
+            Tm[j * nb + j] = tau;
+            psc[j] = scale;
+        }
+        __syncthreads();
+        const T tau = Tm[j * nb + j], scale = psc[j];
+        if (j > 0) {
+            const T sp = psc[j - 1];
+            T* xp = P + (j - 1) * ldp;
+            for (int r = j + tid; r < R; r += nt) xp[r] *= sp;
+        }
+        for (int c = j + 1 + wid; c < pw; c += nw) {
+            T* y = P + c * ldp;
+            if (tau != T(0)) {
+                T s0 = T(0), s1 = T(0);
+                int r = j + 1 + lane;
+                for (; r + 32 < R; r += 64) {
+                    s0 += x[r] * y[r];
+                    s1 += x[r + 32] * y[r + 32];
+                }
+                if (r < R) s0 += x[r] * y[r];
+                const T sdot = warp_sum(s0 + s1) * scale + y[j];
+                const T f = tau * sdot, fs = f * scale;
+                for (int rr = j + 1 + lane; rr < R; rr += 32) y[rr] -= fs * x[rr];
+                __syncwarp();
+                if (lane == 0) y[j] -= f;
             }
-#pragma unroll
-            for (int jj = 0; jj < 4; ++jj) {
-#pragma unroll
-                for (int q = 0; q < 4; ++q) y[jj][q] -= acc[jj][q];
-                if (cok[jj]) st4_col(yc[jj], y[jj], r, R, vec);
+            if (c == j + 1) {
+                __syncwarp();
+                const double t = col_norm2(y, j + 2, R);
+                if (lane == 0) red[(j + 1) & 1] = t;
             }
         }
         __syncthreads();
     }
+    {
+        const int j = pw - 1;
+        const T sp = psc[j];
+        T* xp = P + j * ldp;
+        for (int r = j + 1 + tid; r < R; r += nt) xp[r] *= sp;
+    }
+    __syncthreads();
+}
+
+// T of the compact WY form of the panel (explicit V in P, tau_j on Tm's
+// diagonal): G = V^T V with the tiled product, then row i of T by one lane:
+// T[i][j] = -tau_j sum_{l=i}^{j-1} T[i][l] G[l][j] for j > i (the columnwise
+// recursion of Schreiber & Van Loan, read by rows), zeros below the diagonal.
+template <class T, int NI>
+__device__ void qr_t_matrix(const T* P, int ldp, int R, int pw, T* Tm, int nb, T* G, T* Wp) {
+    for (int cb = 0; cb < pw; cb += QR_QG) {
+        auto col = [&](int c) -> const T* { return cb + c < pw ? P + (cb + c) * ldp : nullptr; };
+        qr_vty<T, NI>(P, ldp, pw, R, Wp, col, true);
+        __syncthreads();
+        const int nw = blockDim.x >> 5;
+        for (int o = threadIdx.x; o < pw * QR_QG; o += blockDim.x) {
+            const int i = o / QR_QG, c = o % QR_QG;
+            if (cb + c < pw) {
+                T s = 0;
+                for (int w = 0; w < nw; ++w) s += Wp[w * 8 * NI * QR_QG + o];
+                G[i * pw + cb + c] = s;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < pw) {
+        const int i = threadIdx.x;
+        for (int j = 0; j < i; ++j) Tm[i * nb + j] = T(0);
+        for (int j = i + 1; j < pw; ++j) {
+            T s = 0;
+            for (int l = i; l < j; ++l) s += Tm[i * nb + l] * G[l * pw + j];
+            Tm[i * nb + j] = -Tm[j * nb + j] * s;
+        }
+    }
+    __syncthreads();
 }
 
 template <class T>
@@ -257,15 +491,6 @@ __device__ __forceinline__ void qr_block_apply_nb(T* A, int ld, int m, int p0, i
         qr_block_apply<T, 1>(A, ld, m, p0, pw, c_begin, c_end, P, ldp, Tm, nbT, Wp, W0, W1, transpose, cm, vec);
 }
 
-// Panel in shared memory as explicit V: zeros above the diagonal, 1 on it.
-template <class T>
-__device__ __forceinline__ void qr_explicit_v(T* P, int ldp, int pw) {
-    for (int o = threadIdx.x; o < pw * pw; o += blockDim.x) {
-        const int i = o / pw, r = o % pw;  // column i, row r
-        if (r <= i) P[i * ldp + r] = (r == i) ? T(1) : T(0);
-    }
-}
-
 template <class T>
 __global__ void __launch_bounds__(QR_THREADS) k_qr(QRJob<T> job) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -276,9 +501,9 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr(QRJob<T> job) {
     T* A = job.A + (long)b * job.strideA;
     T* Tw = job.Tw + (long)b * job.strideT;
     const int* cm = job.colmap ? job.colmap + (long)b * n : nullptr;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
-    const int cap = 8 * qr_ni(nb);
+    const int tid = threadIdx.x, nt = blockDim.x, nw = nt >> 5;
+    const int ni = qr_ni(nb);
+    const int cap = 8 * ni;
     double* red = reinterpret_cast<double*>(smem_raw);
     T* P = reinterpret_cast<T*>(smem_raw + 64 * sizeof(double));
     T* Tm = P + (size_t)nb * ldp;
@@ -298,89 +523,24 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr(QRJob<T> job) {
             P[c * ldp + r] = r < R ? A[(long)QCOL(p0 + c) * ld + p0 + r] : T(0);
         }
         __syncthreads();
-        // --- unblocked factorisation of the panel in shared memory
-        for (int j = 0; j < pw; ++j) {
-            T* x = P + j * ldp;
-            // The squared norm is accumulated in float64: a reflector is orthogonal
-            // only if beta^2 = alpha^2 + ||x||^2 holds to working precision, and a
-            // float32 sum over ~10^3 entries misses that by ~1e-6, which then
-            // compounds through the sweeps.
-            double part = 0.0;
-            for (int r = j + 1 + tid; r < R; r += nt) part += (double)x[r] * (double)x[r];
-            const double xn2 = block_sum(part, red);
-            // reflector parameters: one thread (float64), broadcast through shared memory
-            if (tid == 0) {
-                const double alpha = (double)x[j];
-                double tau = 0.0, scale = 0.0;
-                if (xn2 > 0.0) {
-                    const double beta = -copysign(sqrt(alpha * alpha + xn2), alpha);
-                    tau = (beta - alpha) / beta;
-                    scale = 1.0 / (alpha - beta);
-                    x[j] = T(beta);
-                }
-                red[40] = tau;
-                red[41] = scale;
-                Tm[j * nb + j] = T(tau);
-            }
-            __syncthreads();
-            const double tau = red[40];
-            if (tau != 0.0) {
-                const T scale = T(red[41]);
-                for (int r = j + 1 + tid; r < R; r += nt) x[r] *= scale;
-            }
-            __syncthreads();
-            // apply H_j^T to panel columns j+1 .. pw-1 (one warp per column)
-            if (tau != 0.0) {
-                for (int c = j + 1 + wid; c < pw; c += nw) {
-                    T* y = P + c * ldp;
-                    T s = 0;
-                    for (int r = j + 1 + lane; r < R; r += 32) s += x[r] * y[r];
-                    s = warp_sum(s) + y[j];
-                    const T f = T(tau) * s;
-                    if (lane == 0) y[j] -= f;
-                    for (int r = j + 1 + lane; r < R; r += 32) y[r] -= f * x[r];
-                }
-            }
-            __syncthreads();
-        }
-        // --- T matrix of the panel: T(0:j, j) = -tau_j T(0:j,0:j) V(:,0:j)^T v_j
-        for (int o = tid; o < pw * pw; o += nt) {
-            const int i = o / pw, j = o % pw;
-            if (i < j) {
-                const T* vi = P + i * ldp;
-                const T* vj = P + j * ldp;
-                T s = vi[j];
-                for (int r = j + 1; r < R; ++r) s += vi[r] * vj[r];
-                G[i * pw + j] = s;  // scratch: G holds at least nb*nb entries
-            }
-        }
-        __syncthreads();
-        // column j of T needs columns < j: one step per column, rows in parallel
-        for (int j = 0; j < pw; ++j) {
-            const T tj = Tm[j * nb + j];
-            if (tid < j) {
-                const int i = tid;
-                T s = 0;
-                for (int l = i; l < j; ++l) s += Tm[i * nb + l] * G[l * pw + j];
-                Tm[i * nb + j] = -tj * s;
-            } else if (tid > j && tid < pw) {
-                Tm[tid * nb + j] = 0;
-            }
-            __syncthreads();
-        }
-        // keep T for forming Q; write the factored panel back
-        for (int i = tid; i < nb * nb; i += nt) Tw[(p0 / nb) * nb * nb + i] = Tm[i];
+        qr_panel(P, ldp, R, pw, Tm, nb, W0, red);
+        // write the factored panel (R above, reflectors below the diagonal) back
         for (int i = tid; i < pw * R; i += nt) {
             const int c = i / R, r = i % R;
             A[(long)QCOL(p0 + c) * ld + p0 + r] = P[c * ldp + r];
         }
         __syncthreads();
+        qr_explicit_v(P, ldp, pw);
+        __syncthreads();
+        if (ni == 4) qr_t_matrix<T, 4>(P, ldp, R, pw, Tm, nb, G, Wp);
+        else if (ni == 2) qr_t_matrix<T, 2>(P, ldp, R, pw, Tm, nb, G, Wp);
+        else qr_t_matrix<T, 1>(P, ldp, R, pw, Tm, nb, G, Wp);
+        // keep T for forming Q
+        for (int i = tid; i < nb * nb; i += nt) Tw[(p0 / nb) * nb * nb + i] = Tm[i];
         // --- trailing update of columns p0+pw .. n-1
-        if (p0 + pw < n) {
-            qr_explicit_v(P, ldp, pw);
-            __syncthreads();
+        if (p0 + pw < n)
             qr_block_apply_nb<T>(A, ld, m, p0, pw, p0 + pw, n, P, ldp, Tm, nb, Wp, W0, W1, true, cm, vec);
-        }
+        __syncthreads();
     }
 
     // --- outputs
@@ -415,30 +575,7 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr(QRJob<T> job) {
         __syncthreads();
         if (p0 + pw < kk)
             qr_block_apply_nb<T>(A, ld, m, p0, pw, p0 + pw, kk, P, ldp, Tm, nb, Wp, W0, W1, false, cm, vec);
-        // panel columns in place (unblocked, backwards)
-        for (int j = pw - 1; j >= 0; --j) {
-            const T tj = Tm[j * nb + j];
-            T* x = P + j * ldp;
-            for (int c = j + 1 + wid; c < pw; c += nw) {
-                T* y = P + c * ldp;
-                T s = 0;
-                for (int r = j + 1 + lane; r < R; r += 32) s += x[r] * y[r];
-                s = warp_sum(s) + y[j];
-                const T f = tj * s;
-                if (lane == 0) y[j] -= f;
-                for (int r = j + 1 + lane; r < R; r += 32) y[r] -= f * x[r];
-            }
-            __syncthreads();
-            for (int r = j + 1 + tid; r < R; r += nt) x[r] = -tj * x[r];
-            for (int r = tid; r < j; r += nt) x[r] = 0;
-            if (tid == 0) x[j] = T(1) - tj;
-            __syncthreads();
-        }
-        for (int i = tid; i < pw * m; i += nt) {
-            const int c = i / m, r = i % m;
-            A[(long)QCOL(p0 + c) * ld + r] = (r < p0) ? T(0) : P[c * ldp + (r - p0)];
-        }
-        __syncthreads();
+        qr_form_panel<T>(A, ld, m, p0, pw, P, ldp, Tm, nb, W0, W1, cm, vec);
     }
 }
 
