@@ -205,11 +205,11 @@ struct Plan {
 };
 
 template <class T>
-inline void qr_params(int m, int& nb) {
+inline void qr_params(int m, int n, int& nb) {
     nb = sizeof(T) == 8 ? 16 : 32;  // panel width (at most one warp of reflectors)
     const size_t budget = 220 * 1024;
-    while (nb > 4 && qr_smem_bytes<T>(m, nb) > budget) nb /= 2;
-    if (qr_smem_bytes<T>(m, nb) > budget)
+    while (nb > 4 && qr_smem_bytes<T>(m, nb, n) > budget) nb /= 2;
+    if (qr_smem_bytes<T>(m, nb, n) > budget)
         throw Error(THC_EUNSUPPORTED, "QR column length too large for shared memory");
 }
 
@@ -241,7 +241,7 @@ inline Plan make_plan(int mode, const std::vector<int>& inA, const std::vector<i
         const int m = 4 * P.k[s + 1], n = P.e[s];
         if (s >= 1) {
             int nb;
-            qr_params<T>(m, nb);
+            qr_params<T>(m, n, nb);
             P.maxTw = std::max(P.maxTw, (long)ceil_div(std::min(m, n), nb) * nb * nb);
             P.maxQRm = std::max<long>(P.maxQRm, m);
         }
@@ -257,7 +257,7 @@ inline Plan make_plan(int mode, const std::vector<int>& inA, const std::vector<i
         P.maxN = std::max(P.maxN, n);
         if (m > n) {
             int nb;
-            qr_params<T>(m, nb);
+            qr_params<T>(m, n, nb);
             P.maxTw = std::max(P.maxTw, (long)ceil_div(n, nb) * nb * nb);
             P.maxQRm = std::max<long>(P.maxQRm, m);
         }

@@ -74,7 +74,6 @@ struct Engine {
         opt_in(k_jacobi_select<T, 8>, big);
         opt_in(k_jacobi_select<T, 16>, big);
         opt_in(k_jacobi_select<T, 32>, big);
-        opt_in(k_colsort<T>, big);
         opt_in(k_kinetic_factors, (int)KINETIC_SMEM);
         opt_in(k_krylov_small, (int)KRYLOV_SMEM);
     }
@@ -191,12 +190,13 @@ struct Engine {
                 job.strideT = w.sTw;
                 job.out = w.Lb[s & 1];
                 job.strideOut = w.sL;
-                qr_params<T>(job.m, job.nb);
+                qr_params<T>(job.m, job.n, job.nb);
                 job.mode = QR_L_AND_Q;
                 job.colmap = nullptr;
+                job.pivot = 0;
                 {
                     THC_LAUNCH("qr_lq_sweep", st);
-                    k_qr<T><<<B, QR_THREADS, qr_smem_bytes<T>(job.m, job.nb), st>>>(job);
+                    k_qr<T><<<B, QR_THREADS, qr_smem_bytes<T>(job.m, job.nb, job.n), st>>>(job);
                 }
                 check();
             }
@@ -218,14 +218,11 @@ struct Engine {
             int p = std::min(m, n);
             const int* colmap = nullptr;
             if (m > n) {
-                {
-                    THC_LAUNCH("qr_svd_precond", st);
-                    k_colsort<T><<<B, 256, (size_t)n * sizeof(double), st>>>(w.W, w.sC, m, n, m, w.perm);
-                }
-                check();
+                // block-pivoted QR: the kernel writes the column order it chose to w.perm
                 colmap = w.perm;
                 QRJob<T> job;
-                job.colmap = colmap;
+                job.colmap = w.perm;
+                job.pivot = 1;
                 job.A = w.W;
                 job.strideA = w.sC;
                 job.m = m;
@@ -235,11 +232,11 @@ struct Engine {
                 job.strideT = w.sTw;
                 job.out = w.Z;
                 job.strideOut = w.sZ;
-                qr_params<T>(m, job.nb);
+                qr_params<T>(m, n, job.nb);
                 job.mode = QR_R_ROWS;
                 {
                     THC_LAUNCH("qr_svd_precond", st);
-                    k_qr<T><<<B, QR_THREADS, qr_smem_bytes<T>(m, job.nb), st>>>(job);
+                    k_qr<T><<<B, QR_THREADS, qr_smem_bytes<T>(m, job.nb, n), st>>>(job);
                 }
                 check();
             } else {

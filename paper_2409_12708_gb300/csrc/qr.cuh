@@ -34,8 +34,10 @@ struct QRJob {
     long strideOut;
     int nb;        // panel width
     int mode;
-    const int* colmap;  // optional per-term column permutation (n ints, stride n):
-                        // logical column c is stored in physical column colmap[c]
+    int* colmap;   // optional per-term column permutation (n ints, stride n):
+                   // logical column c is stored in physical column colmap[c]
+    int pivot;     // QR_R_ROWS only: choose the column order by block pivoting
+                   // (colmap is then an output: the chosen order)
 };
 
 // physical column of logical column c under the optional column map cm
@@ -57,10 +59,13 @@ __host__ __device__ inline int qr_ldp(int m) {
 __host__ __device__ inline int qr_ni(int nb) { return nb >= 32 ? 4 : (nb >= 16 ? 2 : 1); }
 
 template <class T>
-__host__ inline size_t qr_smem_bytes(int m, int nb) {
+__host__ inline size_t qr_smem_bytes(int m, int nb, int n) {
     const size_t cap = 8 * qr_ni(nb);  // rows of W per warp partial
-    return 64 * sizeof(double) + (size_t)nb * qr_ldp<T>(m) * sizeof(T) + 2 * (size_t)nb * nb * sizeof(T) +
-           ((size_t)(QR_THREADS / 32) * cap * QR_QG + 2 * cap * QR_QG) * sizeof(T);
+    const size_t base = 64 * sizeof(double) + (size_t)nb * qr_ldp<T>(m) * sizeof(T) + 2 * (size_t)nb * nb * sizeof(T) +
+                        ((size_t)(QR_THREADS / 32) * cap * QR_QG + 2 * cap * QR_QG) * sizeof(T);
+    // pivoting state: nb float64 norms, nb + n metrics / norms, two n-int column maps
+    const size_t piv = (size_t)nb * sizeof(double) + (size_t)(nb + n) * sizeof(T) + 2 * (size_t)n * sizeof(int);
+    return base + ((piv + 15) & ~(size_t)15);
 }
 
 // four consecutive elements with 16-byte accesses (p 16-byte aligned)
@@ -365,26 +370,62 @@ __device__ __forceinline__ void qr_explicit_v(T* P, int ldp, int pw) {
 
 // Unblocked Householder factorisation of the panel P (R rows, zero-padded)
 // with two barriers per column: thread 0 forms reflector j from alpha = P[j][j]
-// and the squared norm below it (computed by warp 0 while it updated the
-// column in the previous step); then every warp applies H_j to its panel
-// columns with the unscaled x (the scale 1/(alpha - beta) is folded into the
-// dot and the update), warp 0 also forms the next column's norm, and all
-// threads scale the previous column, which no longer is read.  tau_j goes to
-// Tm[j][j], beta_j to P[j][j].
+// and the squared norm below it (computed by the warp that updated the column
+// in the previous step); then every warp applies H_j to its panel columns with
+// the unscaled x (the scale 1/(alpha - beta) is folded into the dot and the
+// update), forms the next norm(s), and all threads scale the previous column,
+// which no longer is read.  tau_j goes to Tm[j][j], beta_j to P[j][j].
+// Pivoting (pmp != null, the panel's slice of the column map): before step j
+// thread 0 picks the remaining column with the largest norm below row j-1
+// (alpha^2 + ||x||^2), the columns are swapped in P and in pmp (a third
+// barrier), and every warp keeps the norms of all its columns current.
 template <class T>
-__device__ void qr_panel(T* P, int ldp, int R, int pw, T* Tm, int nb, T* psc, double* red) {
+__device__ void qr_panel(T* P, int ldp, int R, int pw, T* Tm, int nb, T* psc, double* red, int* pmp, double* nb2,
+                         T* met) {
+    __shared__ int ksh;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
-    if (wid == 0) {
-        const double t = col_norm2(P, 1, R);
-        if (lane == 0) red[0] = t;
+    const bool piv = pmp != nullptr;
+    const int R4 = 4 * ceil_div(R, 4);
+    if (!piv) {
+        if (wid == 0) {
+            const double t = col_norm2(P, 1, R);
+            if (lane == 0) red[0] = t;
+        }
+    } else {
+        for (int c = wid; c < pw; c += nw) {
+            const double t = col_norm2(P + c * ldp, 1, R);
+            if (lane == 0) {
+                nb2[c] = t;
+                met[c] = T((double)P[c * ldp] * (double)P[c * ldp] + t);
+            }
+        }
     }
     __syncthreads();
     for (int j = 0; j < pw; ++j) {
         T* x = P + j * ldp;
         if (tid == 0) {
-            const double xn2 = red[j & 1];
-            const T alpha = x[j];
+            int k = j;
+            if (piv) {
+                T best = met[j];
+                for (int c = j + 1; c < pw; ++c)
+                    if (met[c] > best) {
+                        best = met[c];
+                        k = c;
+                    }
+                if (k != j) {
+                    const int ti = pmp[j];
+                    pmp[j] = pmp[k];
+                    pmp[k] = ti;
+                    const double tn = nb2[j];
+                    nb2[j] = nb2[k];
+                    nb2[k] = tn;
+                }
+                ksh = k;
+            }
+            T* xk = P + k * ldp;  // the column that becomes column j
+            const double xn2 = piv ? nb2[j] : red[j & 1];
+            const T alpha = xk[j];
             T tau = T(0), scale = T(0);
             const double a2 = (double)alpha * (double)alpha + xn2;
             // a sub-column below (1e-30)^2 (float32) is treated as zero
@@ -393,25 +434,37 @@ __device__ void qr_panel(T* P, int ldp, int R, int pw, T* Tm, int nb, T* psc, do
                     const T beta = -tcopysign(tsqrt(T(a2)), alpha);
                     tau = (beta - alpha) / beta;
                     scale = T(1) / (alpha - beta);
-                    x[j] = beta;
+                    xk[j] = beta;
                 } else {  // float64 (and float32 columns too small for float32 arithmetic)
                     const double al = alpha;
                     const double beta = -copysign(sqrt(a2), al);
                     tau = T((beta - al) / beta);
                     scale = T(1.0 / (al - beta));
-                    x[j] = T(beta);
+                    xk[j] = T(beta);
                 }
             }
             Tm[j * nb + j] = tau;
             psc[j] = scale;
         }
         __syncthreads();
+        if (piv) {
+            const int k = ksh;
+            if (k != j) {
+                T* xk = P + k * ldp;
+                for (int r = tid; r < R4; r += nt) {
+                    const T t = x[r];
+                    x[r] = xk[r];
+                    xk[r] = t;
+                }
+            }
+        }
         const T tau = Tm[j * nb + j], scale = psc[j];
         if (j > 0) {
             const T sp = psc[j - 1];
             T* xp = P + (j - 1) * ldp;
             for (int r = j + tid; r < R; r += nt) xp[r] *= sp;
         }
+        if (piv) __syncthreads();
         for (int c = j + 1 + wid; c < pw; c += nw) {
             T* y = P + c * ldp;
             if (tau != T(0)) {
@@ -428,7 +481,14 @@ __device__ void qr_panel(T* P, int ldp, int R, int pw, T* Tm, int nb, T* psc, do
                 __syncwarp();
                 if (lane == 0) y[j] -= f;
             }
-            if (c == j + 1) {
+            if (piv) {
+                __syncwarp();
+                const double t = col_norm2(y, j + 2, R);
+                if (lane == 0) {
+                    nb2[c] = t;
+                    met[c] = T((double)y[j + 1] * (double)y[j + 1] + t);
+                }
+            } else if (c == j + 1) {
                 __syncwarp();
                 const double t = col_norm2(y, j + 2, R);
                 if (lane == 0) red[(j + 1) & 1] = t;
@@ -500,8 +560,9 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr(QRJob<T> job) {
     const int ldp = qr_ldp<T>(m);
     T* A = job.A + (long)b * job.strideA;
     T* Tw = job.Tw + (long)b * job.strideT;
-    const int* cm = job.colmap ? job.colmap + (long)b * n : nullptr;
+    const bool piv = job.pivot && job.mode == QR_R_ROWS;
     const int tid = threadIdx.x, nt = blockDim.x, nw = nt >> 5;
+    const int lane = tid & 31, wid = tid >> 5;
     const int ni = qr_ni(nb);
     const int cap = 8 * ni;
     double* red = reinterpret_cast<double*>(smem_raw);
@@ -511,6 +572,18 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr(QRJob<T> job) {
     T* Wp = G + nb * nb;
     T* W0 = Wp + (size_t)nw * cap * QR_QG;
     T* W1 = W0 + (size_t)cap * QR_QG;
+    double* nb2 = reinterpret_cast<double*>(W1 + (size_t)cap * QR_QG);
+    T* met = reinterpret_cast<T*>(nb2 + nb);
+    T* cnrm = met + nb;
+    int* pm = reinterpret_cast<int*>(cnrm + n);
+    int* pm2 = pm + n;
+    // the column map in shared memory: the given one, or the order pivoting chooses
+    {
+        const int* cin = job.colmap ? job.colmap + (long)b * n : nullptr;
+        for (int c = tid; c < n; c += nt) pm[c] = (cin && !piv) ? cin[c] : c;
+    }
+    __syncthreads();
+    const int* cm = pm;
     // 16-byte accesses to columns of A (rows p0 + r, r a multiple of 4)
     const bool vec = ((reinterpret_cast<uintptr_t>(A) & 15) == 0) && (ld % 4 == 0);
 
@@ -518,12 +591,37 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr(QRJob<T> job) {
         const int pw = min(nb, kk - p0);
         const int R = m - p0;
         const int R4 = 4 * ceil_div(R, 4);
+        if (piv) {
+            // block pivoting: order the remaining columns by their norm below row
+            // p0 (ties by position; non-finite norms last), so the panel takes the
+            // largest ones
+            for (int c = p0 + wid; c < n; c += nw) {
+                const T* col = A + (long)pm[c] * ld + p0;
+                T s2 = T(0);
+                for (int r = lane; r < R; r += 32) s2 += col[r] * col[r];
+                s2 = warp_sum(s2);
+                if (lane == 0) cnrm[c] = (s2 == s2) ? s2 : T(-1);
+            }
+            __syncthreads();
+            for (int c = p0 + tid; c < n; c += nt) {
+                const T v = cnrm[c];
+                int rank = 0;
+                for (int q = p0; q < n; ++q) {
+                    const T w = cnrm[q];
+                    rank += (w > v) || (w == v && q < c);
+                }
+                pm2[p0 + rank] = pm[c];
+            }
+            __syncthreads();
+            for (int c = p0 + tid; c < n; c += nt) pm[c] = pm2[c];
+            __syncthreads();
+        }
         for (int i = tid; i < pw * R4; i += nt) {
             const int c = i / R4, r = i % R4;
             P[c * ldp + r] = r < R ? A[(long)QCOL(p0 + c) * ld + p0 + r] : T(0);
         }
         __syncthreads();
-        qr_panel(P, ldp, R, pw, Tm, nb, W0, red);
+        qr_panel(P, ldp, R, pw, Tm, nb, W0, red, piv ? pm + p0 : nullptr, nb2, met);
         // write the factored panel (R above, reflectors below the diagonal) back
         for (int i = tid; i < pw * R; i += nt) {
             const int c = i / R, r = i % R;
@@ -550,6 +648,8 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr(QRJob<T> job) {
             const int r = i / n, c = i % n;
             out[i] = (r <= c && r < kk) ? A[(long)QCOL(c) * ld + r] : T(0);
         }
+        if (piv)
+            for (int c = tid; c < n; c += nt) job.colmap[(long)b * n + c] = pm[c];
         return;
     }
     // QR_L_AND_Q: L = R^T (n x kk)
@@ -576,35 +676,6 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr(QRJob<T> job) {
         if (p0 + pw < kk)
             qr_block_apply_nb<T>(A, ld, m, p0, pw, p0 + pw, kk, P, ldp, Tm, nb, Wp, W0, W1, false, cm, vec);
         qr_form_panel<T>(A, ld, m, p0, pw, P, ldp, Tm, nb, W0, W1, cm, vec);
-    }
-}
-
-// Static column pivoting: perm[c] = index of the column with the c-th largest
-// norm (ties by index).  Ordering the columns by norm before the Householder QR
-// grades the rows of R, which cuts the number of one-sided Jacobi sweeps on R.
-// One CTA per term; A column-major (m x n, ld); dynamic smem: n doubles.
-template <class T>
-__global__ void __launch_bounds__(256) k_colsort(const T* A, long strideA, int m, int n, int ld, int* perm) {
-    extern __shared__ __align__(16) double cn[];
-    const int b = blockIdx.x;
-    A += (long)b * strideA;
-    perm += (long)b * n;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int c = wid; c < n; c += nw) {
-        double acc = 0.0;
-        for (int r = lane; r < m; r += 32) {
-            const double x = A[(long)c * ld + r];
-            acc += x * x;
-        }
-        acc = warp_sum(acc);
-        if (lane == 0) cn[c] = acc;
-    }
-    __syncthreads();
-    for (int c = threadIdx.x; c < n; c += blockDim.x) {
-        const double v = cn[c];
-        int rank = 0;
-        for (int q = 0; q < n; ++q) rank += (cn[q] > v) || (cn[q] == v && q < c);
-        perm[rank] = c;
     }
 }
 
