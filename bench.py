@@ -50,6 +50,7 @@ def parse():
     p.add_argument("--terms", type=int, default=0,
                    help="apply only the first TERMS terms per step (0 = all; for profiling slices)")
     p.add_argument("--no-profile", action="store_true", help="skip the CUDA-event profiled step")
+    p.add_argument("--no-krylov", action="store_true", help="skip the Lanczos step timing")
     return p.parse_args()
 
 
@@ -183,6 +184,46 @@ def ncu_traffic(profile_name, units_per_launch):
                 return None
             return float(f[1]) * units_per_launch
     return None
+
+
+def roofline(prof, stats, models, clocks):
+    """Roofline object of the dominant kernel function of a profiled step.
+
+    prof: {profile name: {"launches", "ms"}} from the library's CUDA-event
+    profile; stats: the Jacobi sweep statistics; models: algorithmic flops per
+    profile name; clocks: the sampled clock summary.  Profile names are grouped
+    by the kernel that runs them (k_qr serves the LQ sweep and the
+    preconditioning QR), the one with the most time is reported against the
+    derived FP32 SIMT peak, with its DRAM traffic from the committed ncu figure.
+    """
+    kernel_of = {"jacobi_svd": "k_jacobi_select", "qr_lq_sweep": "k_qr", "qr_svd_precond": "k_qr"}
+    by_kernel = {}
+    for nm, rec in prof.items():
+        kn = kernel_of.get(nm)
+        if kn is None:
+            continue
+        e = by_kernel.setdefault(kn, {"ms": 0.0, "launches": 0, "flops": 0.0, "names": []})
+        e["ms"] += rec["ms"]
+        e["launches"] += rec["launches"]
+        e["flops"] += models.get(nm, 0.0)
+        e["names"].append(nm)
+    if not by_kernel:
+        return None
+    kname, rec = max(by_kernel.items(), key=lambda kv: kv[1]["ms"])
+    sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    achieved = rec["flops"] / (rec["ms"] / 1e3) / 1e12
+    peak = fp32_alu_peak_tflops(sm_mhz)
+    # matrices (CTAs) per launch: every compression step launches over the same
+    # batch of terms, counted by the Jacobi statistics
+    units = None
+    if "jacobi_sweeps_all" in stats and "jacobi_svd" in prof:
+        units = stats["jacobi_sweeps_all"]["launches"] / max(prof["jacobi_svd"]["launches"], 1)
+    return {"kernel": kname, "profile_names": sorted(rec["names"]), "bound": "alu", "achieved": achieved,
+            "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": ncu_traffic(kname, units),
+            "traffic_unit": "DRAM bytes per launch (ncu, scaled by matrices per launch)",
+            "launches_per_step": rec["launches"], "ms_per_step": rec["ms"],
+            "peak_note": f"derived FP32 SIMT peak: 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz "
+                         "(median SM clock under load)"}
 
 
 def fp32_alu_peak_tflops(sm_mhz, sms=152):
@@ -346,29 +387,29 @@ def run_ours(args):
                 "extrapolated_hpsi_s": s64 * T / n64,
                 "note": f"float64 path timed on terms [0,{n64}) incl. their reuse states, extrapolated"}
 
+    # ---- Krylov step time: 10-step Lanczos on the small L=6, N=12, D=16 workload
+    # (after the timed region; one warm-up run each)
+    krylov = None
+    if not args.no_krylov and rank == 0:
+        tk, ck, zk, pk, Dk = workload("L6_N12_D16")
+        Hk = (dev(tk), dev(ck), dev(zk))
+        krylov = {"workload": "L6_N12_D16", "K": 10}
+        for pth, dtk in (("fp64", torch.float64), ("fp32", torch.float32)):
+            pp = [dev(a, dtk) for a in pk]
+            B.krylov_lanczos_ground(*Hk, pp, 10, Dk, path=pth)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            en, _, _ = B.krylov_lanczos_ground(*Hk, pp, 10, Dk, path=pth)
+            e1.record()
+            e1.synchronize()
+            krylov[pth] = {"s_per_krylov_step": e0.elapsed_time(e1) / 1e3 / 10, "energy": en}
+
     if rank != 0:
         return
     clocks = clk.summary()
     models, n_compress = flop_models(w, D)
-    # dominant kernel by measured time
-    dom = max(prof.items(), key=lambda kv: kv[1]["ms"]) if prof else (None, None)
-    roof = None
-    if dom[0] is not None:
-        name, rec = dom
-        sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
-        flops = models.get(name)
-        if flops is not None:
-            achieved = flops / (rec["ms"] / 1e3) / 1e12
-            peak = fp32_alu_peak_tflops(sm_mhz)
-            units = None
-            if name == "jacobi_svd" and "jacobi_sweeps_all" in stats:
-                units = stats["jacobi_sweeps_all"]["launches"] / max(rec["launches"], 1)  # matrices per launch
-            roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": ncu_traffic(name, units),
-                    "traffic_unit": "DRAM bytes per launch (ncu, scaled by matrices per launch)",
-                    "launches_per_step": rec["launches"], "ms_per_step": rec["ms"],
-                    "peak_note": f"derived FP32 SIMT peak: 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz "
-                                 "(median SM clock under load)"}
+    roof = roofline(prof, stats, models, clocks)
     line = {
         "metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -387,6 +428,7 @@ def run_ours(args):
         "jacobi_sweeps_per_svd": {k: round(v["ms"] / max(v["launches"], 1), 2) for k, v in stats.items()
                                   if k.startswith("jacobi_sweeps")},
         "compressions_per_step": n_compress,
+        "krylov": krylov,
     }
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(args)
