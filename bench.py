@@ -103,8 +103,9 @@ class Clocks:
                 "samples": len(rows), "reasons": reasons}
 
 
-def flop_models(w, D):
-    """Algorithmic flops per kernel class for one full H|psi> (float32 path).
+def flop_models(w, D, n_applied=None):
+    """Algorithmic flops per kernel class for one H|psi> (float32 path) over all
+    terms, or over the first n_applied terms.
 
     Shapes follow the static shape chain of the compression (QR bonds k,
     output bonds chi').  Per-unit models (Golub & Van Loan counts):
@@ -152,12 +153,15 @@ def flop_models(w, D):
             add("svd_finalize", 4.0 * ko * ko * n + 2.0 * m * ko)
         add("gemm_center", 2.0 * out[L - 1] * 4 * k[L - 1])
 
-    T = n_terms(w)
-    # reuse stage 2*2N layer compressions, 2 per term, T-1 reductions (same shapes)
+    T = n_terms(w) if n_applied is None else n_applied
+    # reuse stage: 2 layer compressions per (nu, s') block the applied terms touch
+    # (2N consecutive Coulomb terms share one), 2 per term, T-1 reductions; all
+    # with the same static shapes
     per = {}
     compress(pf)
     per = dict(acc)
-    count = 2 * (2 * N) + 2 * T + (T - 1)
+    slots = -(-min(T, 4 * N * N) // (2 * N))
+    count = 2 * slots + 2 * T + (T - 1)
     return {k: v * count for k, v in per.items()}, count
 
 
@@ -274,6 +278,19 @@ def cpu_baseline(args):
                       f"{n - 1}-add pairwise reduction, numpy float64, {dt:.1f} s"}
 
 
+def combine_replicas(seconds, n_step, steps, world, dist=None, device="cpu"):
+    """Whole-job throughput of `world` independent replicas: every rank timed
+    `steps` steps of n_step terms in `seconds`; the job time is the maximum
+    over ranks (an all-reduce of one float64 when world > 1), and the value is
+    all ranks' terms over that time.  Returns (terms/s, ms per step)."""
+    if world > 1:
+        import torch
+        tt = torch.tensor([seconds], device=device, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        seconds = float(tt)
+    return n_step * steps * world / seconds, seconds / steps * 1e3
+
+
 # ----------------------------------------------------------------------------- our arm
 def run_ours(args):
     import torch
@@ -324,13 +341,8 @@ def run_ours(args):
             ms.append(e0.elapsed_time(e1))
     barrier()
     launches = (B.kernel_launches() - launches0) // max(args.steps, 1)
-    tot = sum(ms) / 1e3
-    if world > 1:
-        tt = torch.tensor([tot], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        tot = float(tt)
-    value = n_step * args.steps * world / tot
-    ms_step = tot / args.steps * 1e3
+    value, ms_step = combine_replicas(sum(ms) / 1e3, n_step, args.steps, world, dist if world > 1 else None,
+                                      "cuda")
 
     # ---- end to end through the public API with host buffers
     e2e = None
@@ -408,7 +420,7 @@ def run_ours(args):
     if rank != 0:
         return
     clocks = clk.summary()
-    models, n_compress = flop_models(w, D)
+    models, n_compress = flop_models(w, D, n_step)
     roof = roofline(prof, stats, models, clocks)
     line = {
         "metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": world, "steps": args.steps,

@@ -96,7 +96,8 @@ typedef struct {
 
 /* Options.  D_max: MPS bond cap after every compression (the paper's M).
  * tol: relative discarded-weight tolerance of the truncation (0 = cap only).
- * term_begin/term_end: half-open range of term indices to apply (-1 = all);
+ * term_begin/term_end: half-open range of term indices to apply (-1 = all;
+ * an empty range is THC_EINVAL);
  * Coulomb terms G_{mu s, nu s'} have index ((s'*N + nu)*2 + s)*N + mu and
  * kinetic terms T_{i s} index 4N^2 + s*L + i.  batch: terms in flight
  * (0 = choose from free memory). */

@@ -43,6 +43,27 @@ __device__ __forceinline__ A block_sum(A v, A* red) {
     return r;
 }
 
+// Block-wide maximum of one non-negative value per thread (NaN ignored);
+// `red` is shared scratch of >= 32 entries.
+__device__ __forceinline__ double block_max(double v, double* red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double r = (threadIdx.x < nw) ? red[threadIdx.x] : 0.0;
+    if (wid == 0)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+    if (threadIdx.x == 0) red[0] = r;
+    __syncthreads();
+    r = red[0];
+    __syncthreads();
+    return r;
+}
+
 __host__ __device__ __forceinline__ int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
 // square root and sign transfer in the storage precision (no silent promotion)

@@ -467,31 +467,37 @@ __global__ void __launch_bounds__(JacobiCfg<T, NPL>::threads) k_jacobi_select(Ja
     __syncthreads();
     const Rows<T> rows{Zs, Zg, ps, n};
     const bool vec = (n % VEC == 0) && ((reinterpret_cast<uintptr_t>(Zg) & 15) == 0);
-    // Frobenius norm (invariant under the rotations): it sets the rounding floor
-    // and a power-of-two scale (exact) that brings it near 1, which keeps every
-    // rotation parameter clear of underflow and overflow
+    // A power-of-two scale (exact) taken from the largest entry brings the
+    // matrix to max |z| in [0.5, 1), which keeps every square, norm and rotation
+    // parameter clear of underflow and overflow whatever the input's magnitude.
+    // The Frobenius norm (invariant under the rotations) of the scaled matrix
+    // then sets the rounding floor.
     __shared__ double red[32];
-    T tpart = T(0);
+    T tmax = T(0);
     for (int r = wid; r < p; r += nw) {
         const T* z = rows(r);
-        for (int c = lane; c < n; c += 32) tpart += z[c] * z[c];
+        for (int c = lane; c < n; c += 32) tmax = fmax(tmax, z[c] < T(0) ? -z[c] : z[c]);
     }
-    const double fro2_in = block_sum((double)tpart, red);
+    const double amax = block_max((double)tmax, red);
     double scale = 1.0;
-    if (fro2_in > 0.0 && fro2_in < 1e300) {
+    if (amax > 0.0 && amax < 1e300) {
         int ex = 0;
-        frexp(fro2_in, &ex);
-        scale = ldexp(1.0, -(ex / 2));
+        frexp(amax, &ex);
+        scale = ldexp(1.0, -ex);
     }
-    if (scale != 1.0) {
+    T tpart = T(0);
+    {
         const T sc = T(scale);
         for (int r = wid; r < p; r += nw) {
             T* z = rows(r);
-            for (int c = lane; c < n; c += 32) z[c] *= sc;
+            for (int c = lane; c < n; c += 32) {
+                const T v = z[c] * sc;
+                z[c] = v;
+                tpart += v * v;
+            }
         }
-        __syncthreads();
     }
-    const double fro2 = fro2_in * scale * scale;
+    const double fro2 = block_sum((double)tpart, red);
     const double floor2 = Real<T>::eps * Real<T>::eps * fro2;
     const int sweeps = jacobi_rows<T, NPL>(rows, p, n, vec, job.rot_tol, floor2, job.max_sweeps, &nrot_sh,
                                            job.status, job.dbg);

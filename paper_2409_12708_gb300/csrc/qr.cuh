@@ -372,7 +372,7 @@ __device__ __forceinline__ void qr_explicit_v(T* P, int ldp, int pw) {
 // with two barriers per column: thread 0 forms reflector j from alpha = P[j][j]
 // and the squared norm below it (computed by the warp that updated the column
 // in the previous step); then every warp applies H_j to its panel columns with
-// the unscaled x (the scale 1/(alpha - beta) is folded into the dot and the
+// the unscaled x (the scale 1/(alpha - beta) is applied inside the dot and the
 // update), forms the next norm(s), and all threads scale the previous column,
 // which no longer is read.  tau_j goes to Tm[j][j], beta_j to P[j][j].
 // Pivoting (pmp != null, the panel's slice of the column map): before step j
@@ -468,14 +468,16 @@ __device__ void qr_panel(T* P, int ldp, int R, int pw, T* Tm, int nb, T* psc, do
         for (int c = j + 1 + wid; c < pw; c += nw) {
             T* y = P + c * ldp;
             if (tau != T(0)) {
+                // x is scaled inside the dot: the product of two raw sub-columns
+                // would underflow in float32 for entries below ~1e-19
                 T s0 = T(0), s1 = T(0);
                 int r = j + 1 + lane;
                 for (; r + 32 < R; r += 64) {
-                    s0 += x[r] * y[r];
-                    s1 += x[r + 32] * y[r + 32];
+                    s0 += (x[r] * scale) * y[r];
+                    s1 += (x[r + 32] * scale) * y[r + 32];
                 }
-                if (r < R) s0 += x[r] * y[r];
-                const T sdot = warp_sum(s0 + s1) * scale + y[j];
+                if (r < R) s0 += (x[r] * scale) * y[r];
+                const T sdot = warp_sum(s0 + s1) + y[j];
                 const T f = tau * sdot, fs = f * scale;
                 for (int rr = j + 1 + lane; rr < R; rr += 32) y[rr] -= fs * x[rr];
                 __syncwarp();

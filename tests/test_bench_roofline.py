@@ -43,3 +43,16 @@ def test_traffic_scaled_by_matrices_and_tied_to_source(tmp_path, monkeypatch):
     assert bench.ncu_traffic("k_qr", None) is None
     src.write_text("kernel v2")  # the kernel changed after the counters were taken
     assert bench.ncu_traffic("k_qr", 320.0) is None
+
+
+def test_flop_model_counts_the_applied_terms():
+    from paper_2409_12708_gb300.workloads import WORKLOADS
+    w = WORKLOADS["L16_N48_D128"]
+    N, T = w["N"], 4 * w["N"] ** 2 + 2 * w["L"]
+    full, c_full = bench.flop_models(w, 128)
+    part, c_part = bench.flop_models(w, 128, 608)
+    # 2 layers for each of the 2N reuse blocks, 2 per term, T - 1 additions
+    assert c_full == 2 * (2 * N) + 2 * T + (T - 1)
+    assert c_part == 2 * 7 + 2 * 608 + 607  # 608 terms touch ceil(608 / 96) = 7 blocks
+    for k in full:
+        assert abs(part[k] / full[k] - c_part / c_full) < 1e-12

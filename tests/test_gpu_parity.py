@@ -277,6 +277,30 @@ def test_lanczos_untruncated_reaches_ED(B):
 
 
 # ------------------------------------------------------------------ edge cases
+@pytest.mark.parametrize("scale", [1.0, 1e-20])
+def test_compress_block_sparse_fp32_at_any_scale(B, scale):
+    """float32 compression of a block-sparse (rank-deficient) state, at unit
+    scale and at 1e-20: the Householder residues and the Jacobi factors then
+    sit where float32 squares underflow, which the column norms (float64
+    fallback), the reflectors (float64 for tiny columns) and the Jacobi
+    (power-of-two scaling) must survive.  The truncation is compared with the
+    oracle's at equal D_max, relative to the state's own norm."""
+    L = 7
+    psi = sector_mps(L, 3, 4, 16, seed=77)
+    psi[-1] = psi[-1] * scale
+    out = B.thc_compress([dev(a, torch.float32) for a in psi], D_max=7, path="fp32")
+    ref = OM.compress(psi, 7)
+    assert rel_dist(to_np(out), ref) < 1e-5
+
+
+def test_empty_term_range_is_rejected(B):
+    t, chi, zeta = thc_hamiltonian(3, 2, seed=5)
+    psi = [dev(a) for a in random_mps(3, 4, seed=6)]
+    with pytest.raises(B.ThcError) as e:
+        B.thc_apply_H(dev(t), dev(chi), dev(zeta), psi, D_max=16, term_begin=5, term_end=5)
+    assert e.value.status == B.EINVAL
+
+
 def test_two_site_chain_and_zero_coefficients(B):
     L = 2
     psi = random_mps(L, 4, seed=3)
