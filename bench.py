@@ -256,8 +256,9 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": v, "unit": "terms/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "L": w["L"], "N": w["N"], "D_max": D,
-                   "terms_per_step": sample},
+        "config": {"workload": args.workload, "L": w["L"], "N": w["N"], "D_max": D, "terms": n_terms(w),
+                   "path": "oracle float64 (timed sample: %d terms per step)" % sample,
+                   "parallelism": "single"},
         "cpu_baseline": {"value": v, "unit": "terms/s", "cores": cores, "kind": "oracle",
                          "sample": f"terms [0,{sample}) of the workload per step (numpy float64 oracle)"},
         "e2e": {"value": v, "unit": "terms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},

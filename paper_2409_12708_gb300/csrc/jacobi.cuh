@@ -81,15 +81,10 @@ __device__ __forceinline__ void static_for(F&& f) {
     }
 }
 
-// Pair maps over the 2R rows one warp holds in registers: K = R disjoint pairs.
-template <int R>
-struct CrossPairs {  // (A_k, B_k): register rows k and R + k (rows moved between steps)
-    static constexpr int K = R;
-    static constexpr int a(int k) { return k; }
-    static constexpr int b(int k) { return R + k; }
-};
+// Pair maps over the 2R rows one warp holds in registers: K = R disjoint pairs
+// per step, all indices compile-time (the steps are unrolled).
 template <int R, int S>
-struct CrossShift {  // step S of the cross pairs in place: A_k with B_{(k+S) mod R}
+struct CrossShift {  // step S of the cross pairs: A_k with B_{(k+S) mod R}
     static constexpr int K = R;
     static constexpr int a(int k) { return k; }
     static constexpr int b(int k) { return R + (k + S) % R; }
@@ -99,16 +94,10 @@ __host__ __device__ constexpr int circle_player(int pos, int r, int P2) {
     return pos == 0 ? 0 : (pos - 1 + r) % (P2 - 1) + 1;
 }
 template <int R, int S>
-struct CircleShift {  // round S of the circle method over the 2R rows in place
+struct CircleShift {  // round S of the circle method over the 2R rows
     static constexpr int K = R;
     static constexpr int a(int k) { return circle_player(k, S, 2 * R); }
     static constexpr int b(int k) { return circle_player(2 * R - 1 - k, S, 2 * R); }
-};
-template <int R>
-struct CirclePairs {  // circle method over 2R positions: k with 2R - 1 - k (rows moved)
-    static constexpr int K = R;
-    static constexpr int a(int k) { return k; }
-    static constexpr int b(int k) { return 2 * R - 1 - k; }
 };
 
 // Launch shape per row length: R rows per block (at most 4, which keeps the
@@ -310,47 +299,23 @@ __device__ __forceinline__ void cta_copy(T* dst, const T* src, long count) {
     }
 }
 
-// Move register rows [lo, hi] one position down, cyclically (row lo goes to
-// position hi), with their norms and validity bits.
-template <class T, int NPL, int NR, int LO, int HI>
-__device__ __forceinline__ void cycle_rows(T (&X)[NR][NPL], T (&nrm)[NR], unsigned& vrows) {
-    T tmp[NPL];
-#pragma unroll
-    for (int i = 0; i < NPL; ++i) tmp[i] = X[LO][i];
-    const T tn = nrm[LO];
-#pragma unroll
-    for (int r = LO; r < HI; ++r) {
-#pragma unroll
-        for (int i = 0; i < NPL; ++i) X[r][i] = X[r + 1][i];
-        nrm[r] = nrm[r + 1];
-    }
-#pragma unroll
-    for (int i = 0; i < NPL; ++i) X[HI][i] = tmp[i];
-    nrm[HI] = tn;
-    constexpr unsigned span = (HI - LO + 1 == 32) ? 0xffffffffu : ((1u << (HI - LO + 1)) - 1u);
-    const unsigned seg = (vrows >> LO) & span;
-    const unsigned rot = (seg >> 1) | ((seg & 1u) << (HI - LO));
-    vrows = (vrows & ~(span << LO)) | (rot << LO);
-}
-
 // One sweep of the block ordering.  Rows are grouped in blocks of R; the
 // blocks play a round-robin tournament, and a warp takes the 2R rows of a
 // block pair (A, B) into registers once per visit, with their squared norms:
 //   * in the first round (where every block plays once) it rotates all pairs
-//     of A u B by the circle method (2R-1 steps of R pairs; unrolled for
-//     R <= 4, otherwise a loop over the fixed pairs (k, 2R-1-k) that moves
-//     rows 1..2R-1 cyclically after each step); this covers the pairs inside
-//     A and inside B;
+//     of A u B by the circle method (2R-1 steps of R pairs), which covers the
+//     pairs inside A and inside B;
 //   * in later rounds it rotates the R^2 cross pairs in R steps, step S pairing
-//     A_k with B_{(k+S) mod R} (unrolled for R <= 4, otherwise a loop over the
-//     fixed pairs (A_k, B_k) that moves the B rows after each step).
-// After a visit every row is back at its position.  Every pair of rows is
-// rotated exactly once per sweep, as in the cyclic method, while each row is
-// read and written once per R rotations instead of once per rotation.  Rows
-// with ||z||^2 <= floor2 are numerically zero (below the rounding level of the
-// matrix they came from) and are not rotated.
+//     A_k with B_{(k+S) mod R}.
+// The steps are unrolled with compile-time pair maps (R <= 4 keeps the code
+// within the instruction cache), so rows never move between registers.  Every
+// pair of rows is rotated exactly once per sweep, as in the cyclic method,
+// while each row is read and written once per R rotations instead of once per
+// rotation.  Rows with ||z||^2 <= floor2 are numerically zero (below the
+// rounding level of the matrix they came from) and are not rotated.
 template <class T, int NPL, int R>
 __device__ int jacobi_sweep_reg(const Rows<T>& rows, int p, int n, bool vec, T rt2, T floor2) {
+    static_assert(R >= 1 && R <= 4, "rows per block");
     const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int nbk = ceil_div(p, R);
     const int P2 = nbk + (nbk & 1);
@@ -379,31 +344,15 @@ __device__ int jacobi_sweep_reg(const Rows<T>& rows, int p, int n, bool vec, T r
 #pragma unroll
                 for (int i = 0; i < 2 * R; ++i) nrm[i] += __shfl_xor_sync(0xffffffffu, nrm[i], o);
             if (rr == 0) {
-                if constexpr (R <= 4) {
-                    static_for<0, 2 * R - 1>([&](auto sc) {
-                        myrot += rotate_regs<T, NPL, 2 * R, CircleShift<R, decltype(sc)::value>>(X, nrm, vrows,
-                                                                                                 rt2, floor2);
-                    });
-                } else {
-#pragma unroll 1
-                    for (int st = 0; st < 2 * R - 1; ++st) {
-                        myrot += rotate_regs<T, NPL, 2 * R, CirclePairs<R>>(X, nrm, vrows, rt2, floor2);
-                        cycle_rows<T, NPL, 2 * R, 1, 2 * R - 1>(X, nrm, vrows);
-                    }
-                }
+                static_for<0, 2 * R - 1>([&](auto sc) {
+                    myrot += rotate_regs<T, NPL, 2 * R, CircleShift<R, decltype(sc)::value>>(X, nrm, vrows, rt2,
+                                                                                             floor2);
+                });
             } else if ((vrows & lowR) && (vrows >> R)) {
-                if constexpr (R <= 4) {
-                    static_for<0, R>([&](auto sc) {
-                        myrot += rotate_regs<T, NPL, 2 * R, CrossShift<R, decltype(sc)::value>>(X, nrm, vrows, rt2,
-                                                                                                floor2);
-                    });
-                } else {
-#pragma unroll 1
-                    for (int st = 0; st < R; ++st) {
-                        myrot += rotate_regs<T, NPL, 2 * R, CrossPairs<R>>(X, nrm, vrows, rt2, floor2);
-                        cycle_rows<T, NPL, 2 * R, R, 2 * R - 1>(X, nrm, vrows);
-                    }
-                }
+                static_for<0, R>([&](auto sc) {
+                    myrot += rotate_regs<T, NPL, 2 * R, CrossShift<R, decltype(sc)::value>>(X, nrm, vrows, rt2,
+                                                                                            floor2);
+                });
             }
 #pragma unroll
             for (int i = 0; i < 2 * R; ++i) {
