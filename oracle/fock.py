@@ -2,7 +2,7 @@
 
 Test infrastructure only (see oracle/__init__.py).
 
-Conventions (paper readings, also listed in the design doc):
+Conventions (readings of the paper where it leaves the choice open):
   * 2L fermionic modes, ordered site-major with spin-up before spin-down
     (App. C: "ordering the spin-up before the spin-down").
   * Two-level mode basis |0>, |1> with |1> occupied; c = [[0,1],[0,0]]

@@ -2,7 +2,7 @@
 
 Test infrastructure only (see oracle/__init__.py).
 
-Readings (the design doc lists them):
+Readings of the paper where it leaves the choice open:
   * Krylov vectors by full Gram-Schmidt: v_{k+1} is the compressed, normalised
     H v_k - sum_{j<=k} <v_j|H v_k> v_j, where the sum is one pairwise
     add-and-compress reduction over [H v_k, -h_0 v_0, ..., -h_k v_k].
@@ -62,14 +62,33 @@ def canonical_orthogonalisation(S):
     return W[:, keep] / np.sqrt(s[keep])
 
 
+def ritz_from_projection(Ht, S):
+    """Eq. eff_H: Ritz values (ascending) of C^H Htil C and the coefficients
+    C y_0 of the lowest Ritz vector on the (non-orthogonal) Krylov vectors."""
+    C = canonical_orthogonalisation(S)
+    Heff = C.conj().T @ Ht @ C
+    e, y = np.linalg.eigh(0.5 * (Heff + Heff.conj().T))
+    return e, C @ y[:, 0]
+
+
+def expm_coefficients(Ht, S, dt):
+    """Eq. Krylov_combination in the C-orthonormalised basis: the coefficients a
+    with sum_i a_i |v_i> = exp(-i dt H) |v_0> projected on span{v_i}; a(0) is
+    the coordinate vector of v_0, C^H S e_0."""
+    C = canonical_orthogonalisation(S)
+    Heff = C.conj().T @ Ht @ C
+    e, y = np.linalg.eigh(0.5 * (Heff + Heff.conj().T))
+    b0 = C.conj().T @ S[:, 0]
+    b = y @ (np.exp(-1j * dt * e) * (y.conj().T @ b0))
+    return C @ b
+
+
 def lanczos_ground(Hop, psi0, K, D_max, tol=0.0):
     """Ritz values (ascending) and ground-state coefficients on the v_i."""
     v, w = krylov_basis(Hop, psi0, K, D_max, tol)
     Ht, S = projected(v, w)
-    C = canonical_orthogonalisation(S)
-    Heff = C.conj().T @ Ht @ C
-    e, y = np.linalg.eigh(0.5 * (Heff + Heff.conj().T))
-    return e, C @ y[:, 0], v
+    e, c = ritz_from_projection(Ht, S)
+    return e, c, v
 
 
 def krylov_expm_step(Hop, psi, dt, K, D_max, tol=0.0):
@@ -77,12 +96,7 @@ def krylov_expm_step(Hop, psi, dt, K, D_max, tol=0.0):
     n0 = M.norm(psi)
     v, w = krylov_basis(Hop, psi, K, D_max, tol)
     Ht, S = projected(v, w)
-    C = canonical_orthogonalisation(S)
-    Heff = C.conj().T @ Ht @ C
-    e, y = np.linalg.eigh(0.5 * (Heff + Heff.conj().T))
-    b0 = C.conj().T @ S[:, 0]
-    b = y @ (np.exp(-1j * dt * e) * (y.conj().T @ b0))
-    a = C @ b
+    a = expm_coefficients(Ht, S, dt)
     out = pairwise_sum([M.scale(v[i], a[i] * n0) for i in range(len(v))], D_max, tol)
     n1 = M.norm(out)
     lost = max(0.0, 1.0 - n1 / n0)

@@ -2,7 +2,7 @@
 
 Test infrastructure only (see oracle/__init__.py).
 
-Term list (readings in the design doc):
+Term list (readings of the paper where it leaves the choice open):
   * Coulomb terms G_{mu sig, nu sig'} (Eq. G), 4 N^2 of them, indexed
         t = ((sig' * N + nu) * 2 + sig) * N + mu
     i.e. mu fastest, then sig, then nu, then sig' (the order of the labels in
