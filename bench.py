@@ -7,8 +7,9 @@ exp(-k/12).
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Prints one JSON line (rank 0).  The headline is the batched float32 path; the
-plain float64 path is timed on a leading subset of terms and reported beside
-it.  Under torchrun every rank runs an independent replica (no collective in
+float32 and plain float64 paths are also timed on the same leading slice of
+terms with the whole slice in flight, with the float32 result's distance from
+the float64 one.  Under torchrun every rank runs an independent replica (no collective in
 the data path); value = terms processed by all ranks / max-over-ranks time.
 """
 from __future__ import annotations
@@ -41,7 +42,9 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default=WORKLOAD)
-    p.add_argument("--fp64-terms", type=int, default=96, help="leading terms timed on the float64 path")
+    p.add_argument("--slice-terms", type=int, default=608,
+                   help="leading terms on which the float32 and float64 paths are compared (same terms, "
+                        "all of them in flight at once)")
     p.add_argument("--cpu-terms", type=int, default=12, help="terms in the oracle's CPU sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -103,73 +106,76 @@ class Clocks:
                 "samples": len(rows), "reasons": reasons}
 
 
+def qr_flops(m, n):
+    """Householder QR of an m x n matrix without forming Q (Golub & Van Loan):
+    sum over the k = min(m, n) reflectors of 4 (m - j)(n - j) = 2mn^2 - 2n^3/3
+    for m >= n."""
+    k = min(m, n)
+    return 4.0 * m * n * k - 2.0 * (m + n) * k * k + 4.0 * k ** 3 / 3.0
+
+
+def svd_flops(m, n):
+    """Singular values and right singular vectors of an m x n matrix
+    (Golub & Van Loan, R-SVD count): 4mn^2 + 8n^3 with the roles of m and n
+    taken so that m >= n."""
+    a, b = max(m, n), min(m, n)
+    return 4.0 * a * b * b + 8.0 * b ** 3
+
+
+# The units of the algorithmic-work model: per compression, the QR sweep's
+# Householder QR of every X_s^T (unit "qr"), the SVD sweep's factorisation of
+# every C_s for sigma and V ("svd", which the library runs as a pivoted QR of C
+# followed by one-sided Jacobi), and the contractions ("gemm").
+UNIT_OF = {"qr_lq_sweep": "qr", "qr_svd_precond": "svd", "jacobi_svd": "svd", "gemm_expand_absorb": "gemm",
+           "gemm_center": "gemm", "gemm_u": "gemm", "svd_finalize": "gemm"}
+KERNELS_OF = {"qr": "k_qr (LQ sweep launches)", "svd": "k_qr (pivoted R-only launches) + k_jacobi_select",
+              "gemm": "k_gemm128 / k_gemm"}
+
+
 def flop_models(w, D, n_applied=None):
-    """Algorithmic flops per kernel class for one H|psi> (float32 path) over all
-    terms, or over the first n_applied terms.
+    """Algorithmic flops per unit class for one H|psi> over all terms, or over
+    the first n_applied terms.
 
     Shapes follow the static shape chain of the compression (QR bonds k,
-    output bonds chi').  Per-unit models (Golub & Van Loan counts):
-      qr_lq_sweep     Householder QR of X^T (m x n) plus forming its Q:
-                      2mn k - (m+n)k^2 + 2k^3/3  +  2m k^2 - 2k^3/3,  k = min(m, n)
-      qr_svd_precond  Householder QR of C (m x n, m > n): 2mn^2 - 2n^3/3
-      jacobi_svd      SVD of the p x n matrix for sigma and V: 4pn^2 + 8n^3
-      gemm_*          2 M N K
+    output bonds chi').  Per compression (one expanded term, Fig. 3):
+      qr    sites L-1..1: Householder QR of X_s^T (m = 4 k_{s+1}, n = e_s), no Q formation
+      svd   sites 0..L-2: sigma and V of C_s (m = 4 chi'_s, n = k_{s+1})
+      gemm  expand+absorb, M Q, U = C V^T, the projector correction: 2 M N K
+    Returns ({unit: flops}, compressions).
     """
     L, N = w["L"], w["N"]
     pf = full_bond_profile(L, D)
-
-    def chain(inA, mode):
-        e = [1] + [(2 * inA[b] if mode == "layer" else 2 * inA[b]) for b in range(1, L)] + [1]
-        k = [1] * (L + 1)
-        for s in range(L - 1, 0, -1):
-            k[s] = min(e[s], 4 * k[s + 1])
-        out = [1] * (L + 1)
-        for s in range(L - 1):
-            out[s + 1] = min(D, 4 * out[s], k[s + 1])
-        return e, k, out
-
-    acc = {}
-
-    def add(name, f):
-        acc[name] = acc.get(name, 0.0) + f
-
-    def compress(inA):
-        e, k, out = chain(inA, "layer")
-        for s in range(L - 1, -1, -1):
-            add("gemm_expand_absorb", 2.0 * (e[s] * 4) * k[s + 1] * e[s + 1])
-            if s >= 1:
-                m, n = 4 * k[s + 1], e[s]
-                kk = min(m, n)
-                add("qr_lq_sweep", 2 * m * n * kk - (m + n) * kk ** 2 + 2 * kk ** 3 / 3
-                    + 2 * m * kk ** 2 - 2 * kk ** 3 / 3)
-        for s in range(L - 1):
-            m, n, ko = 4 * out[s], k[s + 1], out[s + 1]
-            add("gemm_center", 2.0 * out[s] * 4 * n * max(k[s], 1))
-            if m > n:
-                add("qr_svd_precond", 2 * m * n * n - 2 * n ** 3 / 3)
-            p = min(m, n)
-            add("jacobi_svd", 4 * p * n * n + 8 * n ** 3)
-            add("gemm_u", 2.0 * m * ko * n)
-            add("svd_finalize", 4.0 * ko * ko * n + 2.0 * m * ko)
-        add("gemm_center", 2.0 * out[L - 1] * 4 * k[L - 1])
-
+    e = [1] + [2 * pf[b] for b in range(1, L)] + [1]
+    k = [1] * (L + 1)
+    for s in range(L - 1, 0, -1):
+        k[s] = min(e[s], 4 * k[s + 1])
+    out = [1] * (L + 1)
+    for s in range(L - 1):
+        out[s + 1] = min(D, 4 * out[s], k[s + 1])
+    per = {"qr": 0.0, "svd": 0.0, "gemm": 0.0}
+    for s in range(L - 1, -1, -1):
+        per["gemm"] += 2.0 * (e[s] * 4) * k[s + 1] * e[s + 1]
+        if s >= 1:
+            per["qr"] += qr_flops(4 * k[s + 1], e[s])
+    for s in range(L - 1):
+        m, n, ko = 4 * out[s], k[s + 1], out[s + 1]
+        per["gemm"] += 2.0 * out[s] * 4 * n * max(k[s], 1) + 2.0 * m * ko * n + 4.0 * ko * ko * n
+        per["svd"] += svd_flops(m, n)
+    per["gemm"] += 2.0 * out[L - 1] * 4 * k[L - 1]
     T = n_terms(w) if n_applied is None else n_applied
     # reuse stage: 2 layer compressions per (nu, s') block the applied terms touch
     # (2N consecutive Coulomb terms share one), 2 per term, T-1 reductions; all
     # with the same static shapes
-    per = {}
-    compress(pf)
-    per = dict(acc)
     slots = -(-min(T, 4 * N * N) // (2 * N))
     count = 2 * slots + 2 * T + (T - 1)
-    return {k: v * count for k, v in per.items()}, count
+    return {u: v * count for u, v in per.items()}, count
 
 
-def ncu_traffic(profile_name, units_per_launch):
+def ncu_traffic(kernel, units_per_launch):
     """DRAM bytes per launch of a kernel from the committed ncu summary.
 
     profiles/dram_traffic_per_unit.txt holds lines
-    "<profile name> <dram bytes per unit> <unit> <source file> <sha1 of it>"
+    "<kernel key> <dram bytes per unit> <unit> <source file> <sha1 of it>"
     (dram__bytes_read.sum + dram__bytes_write.sum of one captured launch,
     divided by the units it processed).  The figure is used only while the
     kernel source still hashes to the recorded value; otherwise None.
@@ -180,7 +186,7 @@ def ncu_traffic(profile_name, units_per_launch):
         return None
     for line in open(path):
         f = line.split()
-        if len(f) == 5 and f[0] == profile_name:
+        if len(f) == 5 and f[0] == kernel:
             src = os.path.join(ROOT, f[3])
             if not os.path.exists(src):
                 return None
@@ -190,49 +196,74 @@ def ncu_traffic(profile_name, units_per_launch):
     return None
 
 
-def roofline(prof, stats, models, clocks):
-    """Roofline object of the dominant kernel function of a profiled step.
+def fp32_alu_peak_tflops(sm_mhz, sms):
+    """FP32 SIMT peak: sms x 128 FP32 lanes x one FMA (2 flops) per clock."""
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def roofline(prof, stats, models, clocks, sms, peaks=None):
+    """Roofline object of the dominant unit class of a profiled step.
 
     prof: {profile name: {"launches", "ms"}} from the library's CUDA-event
     profile; stats: the Jacobi sweep statistics; models: algorithmic flops per
-    profile name; clocks: the sampled clock summary.  Profile names are grouped
-    by the kernel that runs them (k_qr serves the LQ sweep and the
-    preconditioning QR), the one with the most time is reported against the
-    derived FP32 SIMT peak, with its DRAM traffic from the committed ncu figure.
+    unit class (flop_models); clocks: the sampled clock summary; sms: the
+    device's SM count; peaks: MEASURED_PEAKS.json.  Profile names are grouped
+    into the units of flop_models; the unit with the most time is reported
+    against the derived FP32 SIMT peak (the kernels are SIMT float32), with the
+    TF32 tensor peak (half the measured BF16 sustained rate) beside it.
     """
-    kernel_of = {"jacobi_svd": "k_jacobi_select", "qr_lq_sweep": "k_qr", "qr_svd_precond": "k_qr"}
-    by_kernel = {}
+    by_unit = {}
     for nm, rec in prof.items():
-        kn = kernel_of.get(nm)
-        if kn is None:
+        u = UNIT_OF.get(nm)
+        if u is None:
             continue
-        e = by_kernel.setdefault(kn, {"ms": 0.0, "launches": 0, "flops": 0.0, "names": []})
+        e = by_unit.setdefault(u, {"ms": 0.0, "launches": 0, "names": []})
         e["ms"] += rec["ms"]
         e["launches"] += rec["launches"]
-        e["flops"] += models.get(nm, 0.0)
         e["names"].append(nm)
-    if not by_kernel:
+    if not by_unit:
         return None
-    kname, rec = max(by_kernel.items(), key=lambda kv: kv[1]["ms"])
+    unit, rec = max(by_unit.items(), key=lambda kv: kv[1]["ms"])
     sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
-    achieved = rec["flops"] / (rec["ms"] / 1e3) / 1e12
-    peak = fp32_alu_peak_tflops(sm_mhz)
+    peak = fp32_alu_peak_tflops(sm_mhz, sms)
+    tf32 = 0.5 * peaks["bf16_tflops_sustained"] if peaks and "bf16_tflops_sustained" in peaks else None
+    summary = {}
+    for u, r in by_unit.items():
+        a = models.get(u, 0.0) / (r["ms"] / 1e3) / 1e12
+        summary[u] = {"ms_per_step": r["ms"], "flops_per_step": models.get(u, 0.0), "achieved_tflops": a,
+                      "frac_fp32_simt": a / peak, "frac_tf32_tensor": a / tf32 if tf32 else None,
+                      "profile_names": sorted(r["names"])}
+    achieved = summary[unit]["achieved_tflops"]
     # matrices (CTAs) per launch: every compression step launches over the same
     # batch of terms, counted by the Jacobi statistics
     units = None
     if "jacobi_sweeps_all" in stats and "jacobi_svd" in prof:
         units = stats["jacobi_sweeps_all"]["launches"] / max(prof["jacobi_svd"]["launches"], 1)
-    return {"kernel": kname, "profile_names": sorted(rec["names"]), "bound": "alu", "achieved": achieved,
-            "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": ncu_traffic(kname, units),
-            "traffic_unit": "DRAM bytes per launch (ncu, scaled by matrices per launch)",
-            "launches_per_step": rec["launches"], "ms_per_step": rec["ms"],
-            "peak_note": f"derived FP32 SIMT peak: 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz "
-                         "(median SM clock under load)"}
+    traffic = None
+    if unit == "qr":
+        traffic = ncu_traffic("k_qr", units)
+    elif unit == "svd":
+        a, b = ncu_traffic("k_qr_precond", units), ncu_traffic("k_jacobi_select", units)
+        traffic = a + b if a is not None and b is not None else None
+    return {"kernel": KERNELS_OF[unit], "unit": "TFLOP/s", "work_unit": unit, "bound": "alu",
+            "achieved": achieved, "peak": peak, "frac": achieved / peak,
+            "peak_tensor_tf32": tf32, "frac_tensor_tf32": achieved / tf32 if tf32 else None,
+            "traffic": traffic, "traffic_unit": "DRAM bytes per launch (ncu, scaled by matrices per launch)",
+            "launches_per_step": rec["launches"], "ms_per_step": rec["ms"], "by_unit": summary,
+            "peak_note": f"FP32 SIMT peak derived from the device: {sms} SMs x 128 lanes x 2 flop x "
+                         f"{sm_mhz:.0f} MHz (median SM clock under load); TF32 tensor peak = 1/2 of the "
+                         "measured BF16 sustained rate (MEASURED_PEAKS.json)"}
 
 
-def fp32_alu_peak_tflops(sm_mhz, sms=152):
-    # 128 FP32 lanes per SM, one FMA (2 flops) per lane per clock
-    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+def read_golden(path):
+    """{name: value} from a golden file ("name value" lines, '#' comments)."""
+    vals = {}
+    if os.path.exists(path):
+        for line in open(path):
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()
+                vals[k] = float(v)
+    return vals
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -383,46 +414,72 @@ def run_ours(args):
         B.profile_enable(False)
     stats = {k: prof.pop(k) for k in list(prof) if k.startswith("jacobi_sweeps") or k.startswith("jacobi_budget")}
 
-    # ---- plain float64 per-term path on a leading subset of terms (extrapolated)
+    # ---- float32 vs plain float64 on the same leading slice of terms, every term
+    # of the slice in flight at once on both paths (so both fill the GPU alike);
+    # the float32 result's distance from the float64 one is computed with float64
+    # inner products on the device: |a-b|^2 = <a|a> + <b|b> - 2<a|b>
     fp64 = None
     if not args.no_fp64:
         psi64 = [dev(a) for a in psi]
-        n64 = min(args.fp64_terms, T)
-        B.thc_apply_H(*H, psi64, D_max=D, path="fp64", term_begin=0, term_end=min(n64, 4))
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        B.thc_apply_H(*H, psi64, D_max=D, path="fp64", term_begin=0, term_end=n64)
-        e1.record()
-        e1.synchronize()
-        s64 = e0.elapsed_time(e1) / 1e3
-        fp64 = {"value": n64 / s64, "unit": "terms/s", "terms_timed": n64,
-                "extrapolated_hpsi_s": s64 * T / n64,
-                "note": f"float64 path timed on terms [0,{n64}) incl. their reuse states, extrapolated"}
+        n64 = min(args.slice_terms, T)
+        res = {}
+        for pth, pp in (("fp32", psi32), ("fp64", psi64)):
+            B.thc_apply_H(*H, pp, D_max=D, path=pth, term_begin=0, term_end=min(n64, 8), batch=8)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            o = B.thc_apply_H(*H, pp, D_max=D, path=pth, term_begin=0, term_end=n64, batch=n64)
+            e1.record()
+            e1.synchronize()
+            res[pth] = (e0.elapsed_time(e1) / 1e3, o)
+        a = [x.double() for x in res["fp32"][1]]
+        b = res["fp64"][1]
+        aa, bb, ab = B.mps_inner(a, a), B.mps_inner(b, b), B.mps_inner(a, b)
+        rel = float(np.sqrt(max(aa + bb - 2.0 * ab, 0.0) / bb))
+        s32, s64 = res["fp32"][0], res["fp64"][0]
+        fp64 = {"terms": n64, "in_flight": n64, "fp64_terms_per_s": n64 / s64, "fp32_terms_per_s": n64 / s32,
+                "speedup_fp32_vs_fp64": s64 / s32, "fp32_rel_error_vs_fp64": rel,
+                "extrapolated_fp64_hpsi_s": s64 * T / n64,
+                "note": f"both paths on terms [0,{n64}) with all {n64} terms in flight; float64 H|psi> time "
+                        f"extrapolated from the slice (labelled); relative distance of the float32 result "
+                        f"from the float64 one, float64 inner products on the device"}
 
-    # ---- Krylov step time: 10-step Lanczos on the small L=6, N=12, D=16 workload
-    # (after the timed region; one warm-up run each)
+    # ---- Krylov step time: 10-step Lanczos on the L=6, N=12 workload (after the
+    # timed region; one warm-up run each), at D_max = 16 and untruncated (64);
+    # energies beside the exact ground energy of the (3,3) sector and the dense
+    # 10-step Lanczos value of the same start vector (committed golden file)
     krylov = None
     if not args.no_krylov and rank == 0:
         tk, ck, zk, pk, Dk = workload("L6_N12_D16")
         Hk = (dev(tk), dev(ck), dev(zk))
-        krylov = {"workload": "L6_N12_D16", "K": 10}
+        gold = read_golden(os.path.join(ROOT, "tests", "golden", "config0_energies.txt"))
+        krylov = {"workload": "L6_N12_D16", "K": 10, "ed_ground_energy": gold.get("ed_ground_energy"),
+                  "dense_lanczos_K10": gold.get("dense_lanczos_K10")}
         for pth, dtk in (("fp64", torch.float64), ("fp32", torch.float32)):
-            pp = [dev(a, dtk) for a in pk]
-            B.krylov_lanczos_ground(*Hk, pp, 10, Dk, path=pth)
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            en, _, _ = B.krylov_lanczos_ground(*Hk, pp, 10, Dk, path=pth)
-            e1.record()
-            e1.synchronize()
-            krylov[pth] = {"s_per_krylov_step": e0.elapsed_time(e1) / 1e3 / 10, "energy": en}
+            for Dx in (Dk, 64):
+                pp = [dev(a, dtk) for a in pk]
+                B.krylov_lanczos_ground(*Hk, pp, 10, Dx, path=pth)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                en, _, _ = B.krylov_lanczos_ground(*Hk, pp, 10, Dx, path=pth)
+                e1.record()
+                e1.synchronize()
+                rec = {"s_per_krylov_step": e0.elapsed_time(e1) / 1e3 / 10, "energy": en}
+                if gold:
+                    rec["minus_ed"] = en - gold["ed_ground_energy"]
+                    rec["minus_dense_lanczos_K10"] = en - gold["dense_lanczos_K10"]
+                krylov[f"{pth}_D{Dx}"] = rec
 
     if rank != 0:
         return
     clocks = clk.summary()
     models, n_compress = flop_models(w, D, n_step)
-    roof = roofline(prof, stats, models, clocks)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    peaks = None
+    if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")):
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    roof = roofline(prof, stats, models, clocks, sms, peaks)
     line = {
         "metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -436,7 +493,7 @@ def run_ours(args):
         "roofline": roof,
         "clocks": clocks,
         "fp64": fp64,
-        "speedup_vs_fp64": (value / world) / fp64["value"] if fp64 else None,
+        "speedup_vs_fp64": fp64["speedup_fp32_vs_fp64"] if fp64 else None,
         "kernel_ms_per_step": {k: round(v["ms"], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])},
         "jacobi_sweeps_per_svd": {k: round(v["ms"] / max(v["launches"], 1), 2) for k, v in stats.items()
                                   if k.startswith("jacobi_sweeps")},

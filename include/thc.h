@@ -103,7 +103,10 @@ typedef struct {
  * an empty range is THC_EINVAL);
  * Coulomb terms G_{mu s, nu s'} have index ((s'*N + nu)*2 + s)*N + mu and
  * kinetic terms T_{i s} index 4N^2 + s*L + i.  batch: terms in flight
- * (0 = choose from free memory). */
+ * (0 = choose from free memory).  chunk: at most this many term states are
+ * held before their partial sum is formed (rounded down to a power of two, so
+ * every chunk is a whole subtree of the pairwise reduction and the result does
+ * not depend on it; 0 = as many as a quarter of free memory holds). */
 typedef struct {
     int D_max;
     double tol;
@@ -111,6 +114,7 @@ typedef struct {
     long term_begin;
     long term_end;
     int batch;
+    int chunk;
 } thc_opts;
 
 /* H|psi> as a compressed MPS: Alg. 1 of the paper (the reuse of
@@ -203,19 +207,25 @@ int thc_profile_read(char* buf, int len);
  * allocator, or embedders with a memory budget fixed up front.  The paper has
  * no counterpart; this is a deployment variant of mps_inner.
  *  - Allocates nothing: the scratch (the float64 transfer matrices) is one
- *    file-scope device array of 16 MiB that every GPU loading this library
- *    holds until the process exits.  phi and psi are read in place; real MPS
- *    only (F64 or F32, equal L, d = 4).
+ *    file-scope device array of 16 MiB.  It is reserved on a device when the
+ *    library's module is first used there (lazy module loading, the CUDA
+ *    default) and held until the process exits.  phi and psi are read in
+ *    place; real MPS only (F64 or F32), with the limits of mps_inner (equal L
+ *    in [2, 64], d = 4, bonds in [1, 4096]).
  *  - Limit: 8 * (chi_phi * chi_psi * 5 + 64) bytes (rounded) must fit in
  *    16 MiB, i.e. max bond products up to about 4e5 (512 x 512 works); larger
  *    inputs return THC_EINVAL and nothing is launched.
  *  - The first call on a device looks up the array's device address with that
- *    device current; make that first call before any stream capture.
+ *    device current.  The call reads its result back to the host and
+ *    synchronises `stream`, so it must not be made while `stream` is being
+ *    captured into a CUDA graph: such a call returns THC_EUNSUPPORTED and
+ *    enqueues nothing.
  *  - All calls share the array and it keeps the previous call's contents (the
  *    kernels initialise what they read).  Calls whose GPU work overlaps (other
  *    streams without ordering, other threads) race on it.
  *  - out_re: host pointer; the call synchronises `stream` before returning.
- *    Errors: THC_EINVAL (bad or oversize input), THC_ECUDA; see thc_last_error(). */
+ *    Errors: THC_EINVAL (bad or oversize input), THC_EUNSUPPORTED (stream under
+ *    capture), THC_ECUDA; see thc_last_error(). */
 thc_status mps_inner_noalloc(const thc_mps* phi, const thc_mps* psi, double* out_re, void* stream);
 
 #ifdef __cplusplus

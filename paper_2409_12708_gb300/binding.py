@@ -47,7 +47,8 @@ class thc_hamiltonian(C.Structure):
 
 class thc_opts(C.Structure):
     _fields_ = [("D_max", C.c_int), ("tol", C.c_double), ("path", C.c_int),
-                ("term_begin", C.c_long), ("term_end", C.c_long), ("batch", C.c_int)]
+                ("term_begin", C.c_long), ("term_end", C.c_long), ("batch", C.c_int),
+                ("chunk", C.c_int)]
 
 
 _ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -121,6 +122,17 @@ _FREE_CB = _FREE_FN(_torch_free)
 TORCH_ALLOCATOR = thc_allocator(_ALLOC_CB, _FREE_CB, None)
 
 
+def make_allocator(alloc, free):
+    """A thc_allocator from two Python callables: alloc(bytes, stream) -> int
+    device pointer or None (failure), free(ptr, stream).  The returned object
+    keeps its C callbacks alive."""
+    a = _ALLOC_FN(lambda size, stream, ctx: alloc(int(size), stream))
+    f = _FREE_FN(lambda ptr, stream, ctx: free(ptr, stream))
+    out = thc_allocator(a, f, None)
+    out._keep = (a, f)
+    return out
+
+
 def _stream():
     return C.c_void_p(torch.cuda.current_stream().cuda_stream)
 
@@ -179,8 +191,9 @@ def _ham(t, chi, zeta):
     return h
 
 
-def _opts(D_max, tol, path, term_begin=-1, term_end=-1, batch=0):
-    return thc_opts(int(D_max), float(tol), _PATHS[path], int(term_begin), int(term_end), int(batch))
+def _opts(D_max, tol, path, term_begin=-1, term_end=-1, batch=0, chunk=0):
+    return thc_opts(int(D_max), float(tol), _PATHS[path], int(term_begin), int(term_end), int(batch),
+                    int(chunk))
 
 
 def _code(path):
@@ -188,13 +201,18 @@ def _code(path):
 
 
 # --------------------------------------------------------------------- entry points
-def thc_apply_H(t, chi, zeta, psi, D_max, tol=0.0, path="fp64", term_begin=-1, term_end=-1, batch=0):
+def thc_apply_H(t, chi, zeta, psi, D_max, tol=0.0, path="fp64", term_begin=-1, term_end=-1, batch=0,
+                chunk=0, allocator=None):
     h = _ham(t, chi, zeta)
     d = _desc(psi, _code(path))
-    o = _opts(D_max, tol, path, term_begin, term_end, batch)
+    o = _opts(D_max, tol, path, term_begin, term_end, batch, chunk)
     out = thc_mps()
-    _check(LIB.thc_apply_H(C.byref(h), C.byref(d), C.byref(o), C.byref(out), C.byref(TORCH_ALLOCATOR),
-                           _stream()))
+    al = allocator if allocator is not None else TORCH_ALLOCATOR
+    try:
+        _check(LIB.thc_apply_H(C.byref(h), C.byref(d), C.byref(o), C.byref(out), C.byref(al), _stream()))
+    except ThcError as e:
+        e.out_owner = out.owner  # what the failed call left in the output descriptor
+        raise
     return _take(out)
 
 

@@ -261,7 +261,9 @@ struct Ops {
         // ---- terms, in power-of-two chunks that are exact subtrees of the pairwise reduction
         THC_CUDA(cudaMemGetInfo(&freeb, &totalb));
         long chunk = 1;
-        while (chunk < nT && (double)(2 * chunk) * 1.8 * Pf.size * sizeof(T) < 0.5 * freeb) chunk *= 2;
+        while (chunk < nT && (double)(2 * chunk) * 1.8 * Pf.size * sizeof(T) < 0.5 * freeb &&
+               (o->chunk <= 0 || 2 * chunk <= o->chunk))
+            chunk *= 2;
         const long nchunks = (nT + chunk - 1) / chunk;
         T* chunkres = sc.get<T>((size_t)nchunks * Pf.size);
         for (long ci = 0; ci < nchunks; ++ci) {

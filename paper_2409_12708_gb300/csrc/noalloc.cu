@@ -6,9 +6,15 @@
 // foreign allocations, real-time loops that must not touch the allocator, or
 // embedders whose budget is fixed up front.  mps_inner_noalloc computes the
 // same inner product with its scratch in one file-scope device array of fixed
-// size, reserved when the library is loaded and held by every GPU that loads
-// it until the process exits.  It calls no cudaMalloc/cudaFree and no
-// allocating routine.
+// size.  With lazy module loading (the CUDA default) the array is reserved on
+// a device when this module is first used there, and it stays reserved on
+// that device until the process exits.  The call itself allocates nothing: no
+// cudaMalloc/cudaFree and no allocating routine.
+//
+// The result is read back with a device-to-host copy into a pageable host
+// pointer and a stream synchronisation, neither of which is legal while a
+// stream is being captured into a CUDA graph: a call made on a capturing
+// stream is refused before anything is enqueued.
 //
 // The array's host-side name is only a stand-in for the symbol, not a device
 // address: the device address is obtained once per device with
@@ -137,9 +143,10 @@ extern "C" thc_status mps_inner_noalloc(const thc_mps* phi, const thc_mps* psi, 
         g_noalloc_err = "null argument";
         return THC_EINVAL;
     }
-    if (phi->L != psi->L || phi->L < 1 || phi->L > THC_MAX_SITES || phi->d != 4 || psi->d != 4 ||
+    // the same input limits as mps_inner
+    if (phi->L != psi->L || phi->L < 2 || phi->L > THC_MAX_SITES || phi->d != 4 || psi->d != 4 ||
         phi->dtype != psi->dtype || (phi->dtype != THC_F64 && phi->dtype != THC_F32)) {
-        g_noalloc_err = "phi and psi must be real (F64 or F32) MPS of equal length with d = 4";
+        g_noalloc_err = "phi and psi must be real (F64 or F32) MPS of equal length L in [2, 64] with d = 4";
         return THC_EINVAL;
     }
     if (phi->bond[0] != 1 || psi->bond[0] != 1 || phi->bond[phi->L] != 1 || psi->bond[psi->L] != 1) {
@@ -148,8 +155,8 @@ extern "C" thc_status mps_inner_noalloc(const thc_mps* phi, const thc_mps* psi, 
     }
     int ma = 1, mb = 1;
     for (int b = 0; b <= phi->L; ++b) {
-        if (phi->bond[b] < 1 || psi->bond[b] < 1) {
-            g_noalloc_err = "bond dimensions must be positive";
+        if (phi->bond[b] < 1 || psi->bond[b] < 1 || phi->bond[b] > 4096 || psi->bond[b] > 4096) {
+            g_noalloc_err = "bond dimensions must be in [1, 4096]";
             return THC_EINVAL;
         }
         ma = phi->bond[b] > ma ? phi->bond[b] : ma;
@@ -169,13 +176,26 @@ extern "C" thc_status mps_inner_noalloc(const thc_mps* phi, const thc_mps* psi, 
                         " MiB scratch: needs " + std::to_string(need) + " bytes (max chi_phi*chi_psi ~ 400000)";
         return THC_EINVAL;
     }
+    cudaStream_t s = (cudaStream_t)stream;
+    {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        const cudaError_t e = cudaStreamIsCapturing(s, &cs);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            g_noalloc_err = std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(e);
+            return THC_ECUDA;
+        }
+        if (cs != cudaStreamCaptureStatusNone) {
+            g_noalloc_err = "mps_inner_noalloc cannot run on a stream that is being captured";
+            return THC_EUNSUPPORTED;
+        }
+    }
     void* base = nullptr;
     thc_status st = scratch_address(&base);
     if (st != THC_OK) return st;
     double* E = static_cast<double*>(base);
     double* F = E + nE;
     double* res = F + nF;
-    cudaStream_t s = (cudaStream_t)stream;
     if (phi->dtype == THC_F64) return run<double>(phi, psi, out_re, s, E, F, res);
     return run<float>(phi, psi, out_re, s, E, F, res);
 }

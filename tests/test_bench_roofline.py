@@ -1,5 +1,7 @@
 """Host logic of bench.py's roofline object (no GPU): profile names are grouped
-by kernel function, the dominant one is reported, and the ncu traffic figure is
+into the work units of the flop model (Householder QR of the QR sweep; sigma
+and V of the SVD sweep; contractions), the dominant unit is reported against
+a peak derived from the device's SM count, and the ncu traffic figure is
 scaled by the matrices per launch and dropped when the kernel source changed."""
 import hashlib
 import os
@@ -19,16 +21,30 @@ def _prof():
     return prof, stats
 
 
-def test_dominant_kernel_groups_qr_profile_names():
+def test_flop_units_follow_golub_van_loan():
+    # Householder QR without Q: 2mn^2 - 2n^3/3 (m >= n); the wide case is the transpose
+    assert bench.qr_flops(1024, 256) == 2 * 1024 * 256 ** 2 - 2 * 256 ** 3 / 3
+    assert abs(bench.qr_flops(256, 1024) - bench.qr_flops(1024, 256)) < 1e-3
+    assert bench.qr_flops(1, 1) == 4 - 4 + 4 / 3  # one reflector on one entry
+    # sigma and V: 4mn^2 + 8n^3
+    assert bench.svd_flops(512, 256) == 4 * 512 * 256 ** 2 + 8 * 256 ** 3
+    assert bench.svd_flops(256, 512) == bench.svd_flops(512, 256)
+
+
+def test_dominant_unit_groups_precond_qr_with_jacobi():
     prof, stats = _prof()
-    models = {"jacobi_svd": 5.0e16, "qr_lq_sweep": 3.0e16, "qr_svd_precond": 1.0e16}
-    r = bench.roofline(prof, stats, models, {"sm_mhz": 2070.0})
-    assert r["kernel"] == "k_qr"
-    assert r["profile_names"] == ["qr_lq_sweep", "qr_svd_precond"]
-    assert abs(r["ms_per_step"] - (6063.1 + 2774.4)) < 1e-9
-    assert abs(r["achieved"] - 4.0e16 / ((6063.1 + 2774.4) / 1e3) / 1e12) < 1e-9
-    assert abs(r["peak"] - 152 * 128 * 2 * 2070e6 / 1e12) < 1e-9
+    models = {"svd": 5.0e16, "qr": 3.0e16, "gemm": 1e16}
+    r = bench.roofline(prof, stats, models, {"sm_mhz": 2070.0}, sms=148,
+                       peaks={"bf16_tflops_sustained": 1700.0})
+    assert r["work_unit"] == "svd"
+    assert r["by_unit"]["svd"]["profile_names"] == ["jacobi_svd", "qr_svd_precond"]
+    assert abs(r["ms_per_step"] - (8361.6 + 2774.4)) < 1e-9
+    assert abs(r["achieved"] - 5.0e16 / ((8361.6 + 2774.4) / 1e3) / 1e12) < 1e-9
+    assert abs(r["peak"] - 148 * 128 * 2 * 2070e6 / 1e12) < 1e-9  # SM count from the device
     assert r["frac"] == r["achieved"] / r["peak"]
+    assert r["peak_tensor_tf32"] == 850.0
+    qr = r["by_unit"]["qr"]
+    assert abs(qr["achieved_tflops"] - 3.0e16 / 6.0631 / 1e12) < 1e-9
 
 
 def test_traffic_scaled_by_matrices_and_tied_to_source(tmp_path, monkeypatch):
@@ -56,3 +72,8 @@ def test_flop_model_counts_the_applied_terms():
     assert c_part == 2 * 7 + 2 * 608 + 607  # 608 terms touch ceil(608 / 96) = 7 blocks
     for k in full:
         assert abs(part[k] / full[k] - c_part / c_full) < 1e-12
+    # per compression at D = 128 the sites at full bond count about L - 7 full-size
+    # units (edge sites with smaller bonds as fractions): 8 to 9 QRs of 1024 x 256
+    # and SVDs of 512 x 256
+    assert 8 < full["qr"] / c_full / bench.qr_flops(1024, 256) < 9
+    assert 8 < full["svd"] / c_full / bench.svd_flops(512, 256) < 9

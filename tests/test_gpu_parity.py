@@ -322,3 +322,64 @@ def test_invalid_inputs_raise(B):
     with pytest.raises(B.ThcError) as e:
         B.thc_compress(psi, D_max=4, path="fp32")  # float64 tensors on the float32 path
     assert e.value.status == B.EINVAL
+
+
+# ------------------------------------------------------------------ reduction in chunks
+def test_chunked_reduction_matches_oracle_and_unchunked(B):
+    # 11 terms held at most 4 at a time: three chunks (4, 4 and an odd tail of 3),
+    # each a whole subtree of the pairwise reduction, then a reduction over the
+    # chunk results -- the same tree as one pass, so the result is identical.
+    L, N, D = 5, 3, 8
+    t, chi, zeta = thc_hamiltonian(L, N, seed=21)
+    psi = sector_mps(L, 2, 3, D, seed=22)
+    args = (dev(t), dev(chi), dev(zeta), [dev(a) for a in psi])
+    for t0, t1 in [(3, 14), (30, 41)]:  # Coulomb; Coulomb + kinetic
+        one = B.thc_apply_H(*args, D_max=D, term_begin=t0, term_end=t1)
+        chunked = B.thc_apply_H(*args, D_max=D, term_begin=t0, term_end=t1, chunk=4, batch=3)
+        ref = OT.apply_H(psi, t, chi, zeta, D_max=D, term_begin=t0, term_end=t1)
+        assert rel_dist(to_np(chunked), ref) < 1e-9
+        assert all(torch.equal(a, b) for a, b in zip(one, chunked))
+
+
+# ------------------------------------------------------------------ config 0 energies
+def test_lanczos_L6_N12_untruncated_reaches_ED(B):
+    # the L = 6, N = 12 workload's start state, D_max = 64 (nothing is cut at
+    # L = 6): 40 Krylov vectors reach the exact ground energy of the 400-state
+    # (3, 3) sector of the 4096-dimensional Fock space
+    t, chi, zeta, psi, _ = workload("L6_N12_D16")
+    e, _, _ = B.krylov_lanczos_ground(dev(t), dev(chi), dev(zeta), [dev(a) for a in psi], 40, D_max=64)
+    H = F.hamiltonian_eq1(t, F.thc_v(chi, zeta))
+    assert abs(e - F.ground_energy(H, 6, 3, 3)) < 1e-8
+
+
+@pytest.mark.parametrize("path", ["fp64", "fp32"])
+def test_lanczos_L6_N12_D16_decaying_start_matches_oracle(B, path):
+    # D_max = 16 truncation from a start state whose Schmidt values decay as
+    # exp(-k): the truncations do not cut through near-degenerate singular
+    # values (a 1e-14 perturbation of psi moves the oracle's 10-step energy by
+    # ~1e-10), so energy parity at 1e-8 (float64) is meaningful here
+    t, chi, zeta = thc_hamiltonian(6, 12, seed=0)
+    psi = sector_mps(6, 3, 3, 16, seed=1000, decay=1.0)
+    D, K = 16, 10
+    e, _, _ = B.krylov_lanczos_ground(dev(t), dev(chi), dev(zeta), [dev(a, DT[path]) for a in psi], K,
+                                      D_max=D, path=path)
+    e_ref, _, _ = OK.lanczos_ground(lambda x: OT.apply_H(x, t, chi, zeta, D_max=D), psi, K, D)
+    assert abs(e - e_ref[0]) < (1e-8 if path == "fp64" else 1e-6 * abs(e_ref[0]))
+
+
+# ------------------------------------------------------------------ a full (nu, s') block at full size
+@pytest.fixture(scope="module")
+def block_L16(B):
+    # terms [0, 96) of the L = 16, N = 48, D_max = 128 workload: every (mu, s)
+    # for (nu, s') = (0, up), sharing one reuse state, reduced by the tree
+    t, chi, zeta, psi, D = workload("L16_N48_D128")
+    ref = OT.apply_H(psi, t, chi, zeta, D_max=D, term_begin=0, term_end=96)
+    return t, chi, zeta, psi, D, ref
+
+
+@pytest.mark.parametrize("path,tolr", [("fp64", 1e-9), ("fp32", 1e-6)])
+def test_apply_H_full_block_L16_N48_D128(B, block_L16, path, tolr):
+    t, chi, zeta, psi, D, ref = block_L16
+    out = B.thc_apply_H(dev(t), dev(chi), dev(zeta), [dev(a, DT[path]) for a in psi], D_max=D, path=path,
+                        term_begin=0, term_end=96)
+    assert rel_dist(to_np(out), ref) < tolr

@@ -114,3 +114,18 @@ def test_hubbard_dimer_closed_form(U, tau):
     H = F.hamiltonian_eq1(t, F.thc_v(np.eye(2), U * np.eye(2)))
     e0 = F.ground_energy(H, 2, 1, 1)
     assert np.isclose(e0, U / 2 - np.sqrt(U * U / 4 + 4 * tau * tau) + U, atol=1e-12)
+
+
+def test_config0_golden_energies_are_current():
+    """tests/golden/config0_energies.txt (read by bench.py's Krylov record)
+    equals a fresh oracle computation; 40 dense Lanczos steps reach ED."""
+    import importlib.util
+    path = os.path.join(os.path.dirname(__file__), "golden", "make_config0_energies.py")
+    spec = importlib.util.spec_from_file_location("mk0", path)
+    mk = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mk)
+    stored, fresh = mk.read(), mk.compute()
+    for k in fresh:
+        assert abs(stored[k] - fresh[k]) < 1e-11
+    assert abs(fresh["dense_lanczos_K40"] - fresh["ed_ground_energy"]) < 1e-9
+    assert fresh["dense_lanczos_K10"] > fresh["ed_ground_energy"] + 0.1  # 10 steps are far from converged

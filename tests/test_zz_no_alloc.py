@@ -60,3 +60,33 @@ def test_noalloc_rejects_inputs_beyond_its_scratch(B):
     # a supported call right after the rejection still works
     small = [dev(x, torch.float64) for x in random_mps(6, 8, seed=1)]
     assert abs(B.mps_inner_noalloc(small, small) - B.mps_inner(small, small)) < 1e-10 * B.mps_inner(small, small)
+
+
+def test_noalloc_refuses_a_capturing_stream(B):
+    # it reads its result back and synchronises, which a stream under capture
+    # cannot do: the call is refused before anything is enqueued, and the
+    # capture around it stays valid
+    small = [dev(x, torch.float64) for x in random_mps(6, 8, seed=1)]
+    ref = B.mps_inner(small, small)
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    x = torch.zeros(4, device="cuda")
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            x.add_(1.0)
+            with pytest.raises(B.ThcError) as e:
+                B.mps_inner_noalloc(small, small)
+    assert e.value.status == B.EUNSUPPORTED
+    g.replay()
+    torch.cuda.synchronize()
+    assert float(x.sum()) == 4.0
+    assert abs(B.mps_inner_noalloc(small, small) - ref) < 1e-10 * ref
+
+
+def test_noalloc_accepts_the_inputs_mps_inner_accepts(B):
+    one_site = [torch.ones(1, 4, 1, dtype=torch.float64, device="cuda")]
+    for f in (B.mps_inner, B.mps_inner_noalloc):
+        with pytest.raises(B.ThcError) as e:
+            f(one_site, one_site)  # L = 1 is rejected by both
+        assert e.value.status == B.EINVAL
