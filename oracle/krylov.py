@@ -11,6 +11,10 @@ Readings of the paper where it leaves the choice open:
   * Loss of orthogonality is corrected by a coefficient matrix C (Eq. reortho,
     Eq. eff_H) from canonical orthogonalisation: S = W s W^H, eigenvalues below
     1e-12 * max(s) dropped, C = W s^{-1/2}.
+  * Restart: the next run starts from the lowest Ritz vector sum_i (C y_0)_i v_i,
+    compressed by the pairwise reduction and normalised.  Excited states: the
+    start vector and every Krylov vector are orthogonalised against given lower
+    states within the same Gram-Schmidt sum.
   * Time step: a(dt) = exp(-i dt Heff) a(0) in the orthonormalised basis, with
     a(0) the coordinates of v_0; psi(dt) = sum_i (C a)_i v_i, compressed,
     renormalised to the input norm; the lost norm is reported.
@@ -26,9 +30,23 @@ ORTHO_DROP = 1e-12
 BREAKDOWN = 1e-8  # relative to ||H v_k||: the Krylov space is exhausted
 
 
-def krylov_basis(Hop, psi0, K, D_max, tol):
-    """Return (v, w): K orthogonalised vectors and their compressed images H v."""
-    v = [M.scale(psi0, 1.0 / M.norm(psi0))]
+def orthogonalise_against(x, lower, D_max, tol):
+    """x - sum_m <phi_m|x> phi_m by one pairwise add-and-compress (the lower
+    states phi_m are orthonormal); x itself when there are none."""
+    if not lower:
+        return x
+    items = [x] + [M.scale(f, -M.inner(f, x)) for f in lower]
+    return pairwise_sum(items, D_max, tol)
+
+
+def krylov_basis(Hop, psi0, K, D_max, tol, lower=()):
+    """Return (v, w): K orthogonalised vectors and their compressed images H v.
+
+    With `lower` (orthonormal MPS, e.g. lower eigenstates) the start vector and
+    every new Krylov vector are also orthogonalised against them, in the same
+    Gram-Schmidt sum (excited states, Sec. 2.2)."""
+    x = orthogonalise_against(psi0, list(lower), D_max, tol)
+    v = [M.scale(x, 1.0 / M.norm(x))]
     w = []
     for k in range(K):
         wk = Hop(v[k])
@@ -36,7 +54,8 @@ def krylov_basis(Hop, psi0, K, D_max, tol):
         if k == K - 1:
             break
         h = [M.inner(v[j], wk) for j in range(k + 1)]
-        items = [wk] + [M.scale(v[j], -h[j]) for j in range(k + 1)]
+        g = [M.inner(f, wk) for f in lower]
+        items = [wk] + [M.scale(v[j], -h[j]) for j in range(k + 1)] + [M.scale(f, -gm) for f, gm in zip(lower, g)]
         r = pairwise_sum(items, D_max, tol)
         nr = M.norm(r)
         if nr < BREAKDOWN * M.norm(wk):
@@ -83,12 +102,33 @@ def expm_coefficients(Ht, S, dt):
     return C @ b
 
 
-def lanczos_ground(Hop, psi0, K, D_max, tol=0.0):
+def lanczos_ground(Hop, psi0, K, D_max, tol=0.0, lower=()):
     """Ritz values (ascending) and ground-state coefficients on the v_i."""
-    v, w = krylov_basis(Hop, psi0, K, D_max, tol)
+    v, w = krylov_basis(Hop, psi0, K, D_max, tol, lower)
     Ht, S = projected(v, w)
     e, c = ritz_from_projection(Ht, S)
     return e, c, v
+
+
+def ritz_vector(c, v, D_max, tol=0.0):
+    """sum_i c_i |v_i> by the pairwise reduction, normalised."""
+    x = pairwise_sum([M.scale(v[i], c[i]) for i in range(len(v))], D_max, tol)
+    return M.scale(x, 1.0 / M.norm(x))
+
+
+def lanczos_restarted(Hop, psi0, K, cycles, D_max, tol=0.0, lower=()):
+    """Restarted Lanczos (Sec. 2.2): `cycles` runs of K-step Lanczos, each
+    started from the previous run's lowest Ritz vector (compressed and
+    normalised).  With `lower` states every run stays orthogonal to them, so the
+    lowest Ritz value approximates the next eigenvalue above them.  Returns the
+    lowest Ritz value of every cycle and the last Ritz vector."""
+    x = psi0
+    energies = []
+    for _ in range(cycles):
+        e, c, v = lanczos_ground(Hop, x, K, D_max, tol, lower)
+        energies.append(e[0])
+        x = ritz_vector(c, v, D_max, tol)
+    return np.array(energies), x
 
 
 def krylov_expm_step(Hop, psi, dt, K, D_max, tol=0.0):

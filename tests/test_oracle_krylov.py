@@ -191,3 +191,104 @@ def test_config0_D16_random_start_is_ill_conditioned():
     p2[2] = p2[2] * (1 + 1e-14 * np.random.default_rng(5).standard_normal(p2[2].shape))
     e2, _, _ = KR.lanczos_ground(Hop, p2, 10, D)
     assert abs(e[0] - e2[0]) > 1e-5
+
+
+# --------------------------------------------------------------------------
+# Restarted Lanczos and excited states (Sec. 2.2: restart from the Ritz
+# vector; an excited state from a start vector orthogonal to the lower ones)
+
+def _dense_restarted(H, v0, K, cycles, lower=()):
+    """Textbook restarted Lanczos on dense vectors: K-step Lanczos with full
+    reorthogonalisation (also against `lower`), restart from the lowest Ritz
+    vector."""
+    def orth(w, basis):
+        for _ in range(2):
+            for b in basis:
+                w = w - np.vdot(b, w) * b
+        return w
+    x, out = v0, []
+    for _ in range(cycles):
+        V = [orth(x, lower)]
+        V[0] = V[0] / np.linalg.norm(V[0])
+        for _ in range(K - 1):
+            w = orth(H @ V[-1], list(lower) + V)
+            V.append(w / np.linalg.norm(w))
+        Vm = np.array(V).T
+        e, y = np.linalg.eigh(Vm.T @ H @ Vm)
+        out.append(e[0])
+        x = Vm @ y[:, 0]
+    return np.array(out)
+
+
+def _mps_from_dense(vec, L):
+    """Exact MPS of a dense 4^L vector by successive SVDs (no truncation)."""
+    sites, rest, left = [], vec.reshape(1, -1), 1
+    for _ in range(L - 1):
+        m = rest.reshape(left * 4, -1)
+        u, s, vh = np.linalg.svd(m, full_matrices=False)
+        k = int(np.sum(s > 1e-14 * s[0]))
+        sites.append(u[:, :k].reshape(left, 4, k))
+        rest, left = s[:k, None] * vh[:k], k
+    sites.append(rest.reshape(left, 4, 1))
+    return sites
+
+
+def test_restarted_lanczos_untruncated_matches_dense_and_reaches_ED():
+    L = 4
+    t, chi, zeta = thc_hamiltonian(L, 3, seed=40)
+    H = F.hamiltonian_eq1(t, F.thc_v(chi, zeta))
+    psi = sector_mps(L, 2, 2, 256, seed=41)
+    Hop = lambda x: TH.apply_H(x, t, chi, zeta, D_max=10 ** 6)
+    e, x = KR.lanczos_restarted(Hop, psi, 4, 8, D_max=10 ** 6)
+    s = F.sector(L, 2, 2)
+    ref = _dense_restarted(H[s][:, s].toarray(), M.to_dense(psi)[s], 4, 8)
+    assert np.allclose(e, ref, atol=1e-9)
+    assert np.all(np.diff(e) <= 1e-10)  # each restart keeps the previous Ritz vector in its space
+    E = np.linalg.eigvalsh(H[s][:, s].toarray())
+    assert abs(e[-1] - E[0]) < 1e-6
+    assert abs(M.norm(x) - 1.0) < 1e-12
+
+
+def test_excited_state_from_orthogonalised_lanczos():
+    # Dense tensors conserve (N_up, N_dn) only up to rounding: over many restarts
+    # the rounding noise in other particle-number sectors, which hold lower
+    # levels, is amplified by the Krylov iteration (the paper's block-sparse
+    # tensors conserve the sector exactly): here a third cycle of 12 vectors
+    # already falls to the lowest level of another sector.  Two cycles of 12
+    # converge to 2e-7, before that noise has grown.
+    L = 4
+    t, chi, zeta = thc_hamiltonian(L, 3, seed=41)
+    H = F.hamiltonian_eq1(t, F.thc_v(chi, zeta))
+    s = F.sector(L, 2, 2)
+    E, Y = np.linalg.eigh(H[s][:, s].toarray())
+    g = np.zeros(4 ** L)
+    g[s] = Y[:, 0]
+    ground = _mps_from_dense(g, L)
+    psi = sector_mps(L, 2, 2, 256, seed=43)
+    Hop = lambda x: TH.apply_H(x, t, chi, zeta, D_max=10 ** 6)
+    e, x = KR.lanczos_restarted(Hop, psi, 12, 2, D_max=10 ** 6, lower=[ground])
+    ref = _dense_restarted(H[s][:, s].toarray(), M.to_dense(psi)[s], 12, 2, lower=[Y[:, 0]])
+    assert np.allclose(e, ref, atol=1e-9)
+    assert abs(e[-1] - E[1]) < 1e-6  # the first excited level of the sector
+    assert abs(M.inner(ground, x)) < 1e-10
+
+
+def test_truncated_lanczos_amplifies_per_step_errors():
+    """L = 6, N = 12, D_max = 16, 10 steps from a decaying-spectrum start (the
+    case the float64 GPU path matches to 1e-8): rounding psi to float32 once
+    moves the oracle's energy by only ~4e-8, but an error of 2e-6 in every
+    H v_k -- the float32 path's measured H|psi> error at this size -- moves it
+    by ~1e-3, because each Gram-Schmidt sum is truncated to D_max before its
+    cancellations complete.  Energies of the float32 path on truncated Krylov
+    runs are therefore compared with the oracle only at that level."""
+    t, chi, zeta = thc_hamiltonian(6, 12, seed=0)
+    psi = sector_mps(6, 3, 3, 16, seed=1000, decay=1.0)
+    e0, _, _ = KR.lanczos_ground(lambda x: TH.apply_H(x, t, chi, zeta, D_max=16), psi, 10, 16)
+    rng = np.random.default_rng(2)
+
+    def Hop(x):
+        y = TH.apply_H(x, t, chi, zeta, D_max=16)
+        return [a * (1 + 2e-6 * rng.standard_normal(a.shape)) for a in y]
+
+    e, _, _ = KR.lanczos_ground(Hop, psi, 10, 16)
+    assert abs(e[0] - e0[0]) > 1e-4
