@@ -58,11 +58,20 @@ typedef enum {
 /* Storage dtype of MPS site tensors. */
 typedef enum { THC_F64 = 0, THC_F32 = 1, THC_C64 = 2, THC_C128 = 3 } thc_dtype;
 
-/* Compute path.  FP64: every step in float64 ("plain FP64 path").  FP32: site
- * tensors, contractions, QR and Jacobi SVD in float32; singular values are
- * accumulated and the truncation decided in float64; inner products and the
- * Krylov projected problems are float64. */
-typedef enum { THC_PATH_FP64 = 0, THC_PATH_FP32 = 1 } thc_path;
+/* Compute path.  FP64: every step in float64 ("plain FP64 path"); site tensors
+ * F64, or C128 for complex MPS.  FP32: site tensors (F32 or C64),
+ * contractions, QR and Jacobi SVD in float32; singular values are accumulated
+ * and the truncation decided in float64; inner products and the Krylov
+ * projected problems are float64.  Complex MPS (the states of a time
+ * evolution, Sec. 2.2) take the same steps with complex Householder
+ * reflectors, complex one-sided Jacobi rotations and conjugation on the bra;
+ * they are supported up to D_max = 256 (THC_EUNSUPPORTED above).
+ * TF32: FP32 storage (F32 or C64) and steps, except that the contractions of
+ * the compression (the expand-and-absorb, centre, U and projector products)
+ * of real MPS run on the tensor cores as error-compensated TF32 (each float32
+ * operand split into two TF32 numbers, three products accumulated in float32,
+ * Ootomo & Yokota 2022), which keeps float32 accuracy. */
+typedef enum { THC_PATH_FP64 = 0, THC_PATH_FP32 = 1, THC_PATH_TF32 = 2 } thc_path;
 
 /* Stream-ordered allocator supplied by the caller (e.g. PyTorch's caching
  * allocator).  alloc returns NULL on failure. */
@@ -122,8 +131,8 @@ typedef struct {
  * the bond-2 ladder MPOs of the elementary-MPO equations is applied and
  * followed by the QR-then-SVD compression of Fig. 3, and the compressed terms
  * are summed by the pairwise reduction of Sec. 4.5.  psi must have dtype
- * F64 (path FP64) or F32 (path FP32).  `out` receives a library-owned MPS of
- * the same dtype whose bonds are at most D_max. */
+ * F64 or C128 (path FP64), F32 or C64 (path FP32).  `out` receives a
+ * library-owned MPS of the same dtype whose bonds are at most D_max. */
 thc_status thc_apply_H(const thc_hamiltonian* H, const thc_mps* psi, const thc_opts* opts,
                        thc_mps* out, const thc_allocator* alloc, void* stream);
 
@@ -139,14 +148,17 @@ thc_status thc_layer_apply(const thc_mps* psi, const double* coef, int sigma, in
 thc_status thc_compress(const thc_mps* psi, const thc_opts* opts, thc_mps* out,
                         const thc_allocator* alloc, void* stream);
 
-/* <phi|psi> = sum conj(phi) psi by transfer matrices, accumulated in float64.
- * out_re / out_im: host pointers (out_im may be NULL for real states). */
+/* <phi|psi> = sum conj(phi) psi by transfer matrices, accumulated in float64
+ * (complex float64 for complex MPS).  phi and psi share L and dtype.
+ * out_re / out_im: host pointers (out_im may be NULL; 0 for real states). */
 thc_status mps_inner(const thc_mps* phi, const thc_mps* psi, double* out_re, double* out_im,
                      void* stream);
 
 /* compress(sum_i coeff_i |x_i>): direct sums and compressions of the pairwise
  * reduction (Sec. 3.2, Sec. 4.5).  coeff_re/coeff_im: host float64 [n]
- * (coeff_im may be NULL).  All xs share L and dtype. */
+ * (coeff_im may be NULL; non-zero imaginary parts need complex MPS, else
+ * THC_EINVAL).  All xs share L and dtype; their bonds are at most
+ * min(D_max, 4^b, 4^(L-b)). */
 thc_status mps_add_compress(int n, const double* coeff_re, const double* coeff_im,
                             const thc_mps* const* xs, const thc_opts* opts, thc_mps* out,
                             const thc_allocator* alloc, void* stream);
@@ -161,10 +173,42 @@ thc_status krylov_lanczos_ground(const thc_hamiltonian* H, const thc_mps* psi0, 
                                  const thc_opts* opts, double* energy, double* ritz,
                                  thc_mps* ground, const thc_allocator* alloc, void* stream);
 
-/* One global-Krylov time step (Sec. 2.2, Eq. Krylov_combination):
- * a(dt) = exp(-i dt Heff) a(0), psi(dt) = compress(sum_i a_i v_i) renormalised
- * to the norm of psi; lost_norm (host, may be NULL) = 1 - ||psi(dt)||/||psi||
- * before renormalisation.  `out` is complex (C128 for path FP64, C64 for FP32). */
+/* Restarted Lanczos and excited states (Sec. 2.2: restarting improves the
+ * convergence under truncation; an excited state follows from a start vector
+ * orthogonal to the lower eigenstates).  `cycles` runs of the Lanczos of
+ * krylov_lanczos_ground with K vectors each, every run started from the
+ * previous run's lowest Ritz vector (its pairwise-reduced combination of the
+ * v_i, normalised).  lower[0..n_lower-1]: optional orthonormal MPS (e.g. lower
+ * eigenstates; same L and dtype as psi0, bonds at most min(D_max, 4^b,
+ * 4^(L-b))): the start vector and every Krylov vector are orthogonalised
+ * against them within the same Gram-Schmidt sum, so the lowest Ritz value
+ * approximates the next level above them.  energies: host double[cycles],
+ * the lowest Ritz value of each run; state: optional output MPS (psi0's
+ * dtype), the last Ritz vector (NULL to skip).  Dense tensors conserve
+ * (N_up, N_dn) only to rounding: over many Krylov vectors rounding noise in
+ * other particle-number sectors can grow toward their lower levels.
+ * Errors as krylov_lanczos_ground; THC_EINVAL for cycles < 1 or bad lower
+ * states. */
+thc_status krylov_lanczos_restarted(const thc_hamiltonian* H, const thc_mps* psi0, int K, int cycles,
+                                    int n_lower, const thc_mps* const* lower, const thc_opts* opts,
+                                    double* energies, thc_mps* state, const thc_allocator* alloc,
+                                    void* stream);
+
+/* One global-Krylov time step (Sec. 2.2, Eq. Krylov_combination): K Krylov
+ * vectors v_i from psi/|psi| (Gram-Schmidt by mps_add_compress, as
+ * krylov_lanczos_ground), the projected Htil and S, the correction of
+ * Eq. reortho / Eq. eff_H by canonical orthogonalisation, and
+ * a(dt) = exp(-i dt Heff) a(0) in the orthonormalised basis (a complex
+ * Hermitian float64 eigensolver on the device); then
+ * psi(dt) = compress(sum_i |psi| a_i v_i) by the pairwise reduction,
+ * renormalised to |psi|.  psi: real or complex MPS of the path's precision
+ * (a real psi is converted to complex first), bonds at most
+ * min(D_max, 4^b, 4^(L-b)); D_max <= 256.  lost_norm (host, may be NULL) =
+ * 1 - |psi(dt)|/|psi| before the renormalisation.  `out` receives a
+ * library-owned complex MPS (C128 for path FP64, C64 for FP32).
+ * Errors: THC_EINVAL (bad input, dt not finite), THC_EUNSUPPORTED (bonds or
+ * D_max out of range), THC_EBREAKDOWN (psi = 0), THC_ETIMEOUT (the small
+ * eigensolver ran out of sweeps). */
 thc_status krylov_expm_apply(const thc_hamiltonian* H, const thc_mps* psi, double dt, int K,
                              const thc_opts* opts, thc_mps* out, double* lost_norm,
                              const thc_allocator* alloc, void* stream);

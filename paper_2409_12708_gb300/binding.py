@@ -7,7 +7,8 @@ site tensors.  There is no CPU fallback: if the library is missing, importing
 this module raises.
 
 An MPS is a list of L CUDA tensors, site i of shape [chi_i, 4, chi_{i+1}]
-(float64 for path "fp64", float32 for path "fp32").
+(float64 or complex128 for path "fp64", float32 or complex64 for paths "fp32"
+and "tf32"; "tf32" runs the compression's contractions on the tensor cores).
 """
 from __future__ import annotations
 
@@ -22,10 +23,11 @@ LIB_PATH = os.path.join(_HERE, "lib", "libthc.so")
 MAX_SITES = 64
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, EBREAKDOWN, EUNSUPPORTED = range(8)
 F64, F32, C64, C128 = range(4)
-PATH_FP64, PATH_FP32 = 0, 1
-_PATHS = {"fp64": PATH_FP64, "fp32": PATH_FP32}
-_DT = {PATH_FP64: (F64, torch.float64), PATH_FP32: (F32, torch.float32)}
-_TORCH_OF = {F64: torch.float64, F32: torch.float32}
+PATH_FP64, PATH_FP32, PATH_TF32 = 0, 1, 2
+_PATHS = {"fp64": PATH_FP64, "fp32": PATH_FP32, "tf32": PATH_TF32}
+_DT = {PATH_FP64: (F64, torch.float64), PATH_FP32: (F32, torch.float32), PATH_TF32: (F32, torch.float32)}
+_TORCH_OF = {F64: torch.float64, F32: torch.float32, C64: torch.complex64, C128: torch.complex128}
+_TYPESTR = {F64: "<f8", F32: "<f4", C64: "<c8", C128: "<c16"}
 
 
 class ThcError(RuntimeError):
@@ -74,6 +76,9 @@ def _load():
                              P(thc_mps), P(thc_allocator), C.c_void_p],
         "krylov_lanczos_ground": [P(thc_hamiltonian), P(thc_mps), C.c_int, P(thc_opts), P(C.c_double),
                                   P(C.c_double), P(thc_mps), P(thc_allocator), C.c_void_p],
+        "krylov_lanczos_restarted": [P(thc_hamiltonian), P(thc_mps), C.c_int, C.c_int, C.c_int,
+                                     P(P(thc_mps)), P(thc_opts), P(C.c_double), P(thc_mps), P(thc_allocator),
+                                     C.c_void_p],
         "krylov_expm_apply": [P(thc_hamiltonian), P(thc_mps), C.c_double, C.c_int, P(thc_opts),
                               P(thc_mps), P(C.c_double), P(thc_allocator), C.c_void_p],
         "thc_kinetic_factors": [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
@@ -101,7 +106,7 @@ LIB = _load()
 EXPORTED = ("thc_apply_H", "thc_layer_apply", "thc_compress", "mps_inner", "mps_add_compress",
             "krylov_lanczos_ground", "krylov_expm_apply", "thc_kinetic_factors", "thc_mps_free",
             "thc_last_error", "thc_build_info", "thc_kernel_launches", "thc_profile_enable",
-            "thc_profile_read", "mps_inner_noalloc")
+            "thc_profile_read", "mps_inner_noalloc", "krylov_lanczos_restarted")
 
 
 # --------------------------------------------------------------------- allocator
@@ -143,7 +148,7 @@ def _check(status):
 
 
 # --------------------------------------------------------------------- marshalling
-_CODE_OF = {torch.float64: F64, torch.float32: F32}
+_CODE_OF = {torch.float64: F64, torch.float32: F32, torch.complex64: C64, torch.complex128: C128}
 
 
 def _desc(sites, dtype_code=None):
@@ -171,8 +176,7 @@ class _View:
 
 def _take(m):
     """Copy a library-owned output MPS into torch tensors and release the block."""
-    tdt = _TORCH_OF[m.dtype]
-    typestr = "<f8" if tdt == torch.float64 else "<f4"
+    typestr = _TYPESTR[m.dtype]
     out = []
     for i in range(m.L):
         shape = (m.bond[i], 4, m.bond[i + 1])
@@ -236,11 +240,11 @@ def thc_compress(psi, D_max, tol=0.0, path="fp64"):
 
 
 def mps_inner(phi, psi):
-    code = F64 if phi[0].dtype == torch.float64 else F32
-    a, b = _desc(phi, code), _desc(psi, code)
+    """<phi|psi> (conjugating phi); a float for real MPS, a complex for complex MPS."""
+    a, b = _desc(phi), _desc(psi)
     re, im = C.c_double(), C.c_double()
     _check(LIB.mps_inner(C.byref(a), C.byref(b), C.byref(re), C.byref(im), _stream()))
-    return re.value
+    return complex(re.value, im.value) if phi[0].is_complex() else re.value
 
 
 def mps_inner_noalloc(phi, psi):
@@ -257,10 +261,11 @@ def mps_add_compress(coeffs, xs, D_max, tol=0.0, path="fp64"):
     n = len(xs)
     descs = [_desc(x, _code(path)) for x in xs]
     arr = (C.POINTER(thc_mps) * n)(*[C.pointer(d) for d in descs])
-    cre = (C.c_double * n)(*[float(c) for c in coeffs])
+    cre = (C.c_double * n)(*[complex(c).real for c in coeffs])
+    cim = (C.c_double * n)(*[complex(c).imag for c in coeffs])
     o = _opts(D_max, tol, path)
     out = thc_mps()
-    _check(LIB.mps_add_compress(n, cre, None, arr, C.byref(o), C.byref(out), C.byref(TORCH_ALLOCATOR),
+    _check(LIB.mps_add_compress(n, cre, cim, arr, C.byref(o), C.byref(out), C.byref(TORCH_ALLOCATOR),
                                 _stream()))
     return _take(out)
 
@@ -279,7 +284,26 @@ def krylov_lanczos_ground(t, chi, zeta, psi0, K, D_max, tol=0.0, path="fp64", wa
     return e.value, [ritz[i] for i in range(K)], ground
 
 
+def krylov_lanczos_restarted(t, chi, zeta, psi0, K, cycles, D_max, lower=(), tol=0.0, path="fp64",
+                             want_state=False):
+    """Restarted Lanczos (optionally orthogonal to `lower` states); returns
+    (lowest Ritz value of every cycle, last Ritz vector or None)."""
+    h = _ham(t, chi, zeta)
+    d = _desc(psi0, _code(path))
+    lows = [_desc(x, _code(path)) for x in lower]
+    arr = (C.POINTER(thc_mps) * max(len(lows), 1))(*[C.pointer(x) for x in lows])
+    o = _opts(D_max, tol, path)
+    en = (C.c_double * cycles)()
+    g = thc_mps()
+    _check(LIB.krylov_lanczos_restarted(C.byref(h), C.byref(d), int(K), int(cycles), len(lows), arr, C.byref(o),
+                                        en, C.byref(g) if want_state else None, C.byref(TORCH_ALLOCATOR),
+                                        _stream()))
+    return [en[i] for i in range(cycles)], (_take(g) if want_state else None)
+
+
 def krylov_expm_apply(t, chi, zeta, psi, dt, K, D_max, tol=0.0, path="fp64"):
+    """One Krylov time step; psi real or complex, the result complex
+    (complex128 on path "fp64", complex64 on "fp32"); returns (psi(dt), lost_norm)."""
     h = _ham(t, chi, zeta)
     d = _desc(psi, _code(path))
     o = _opts(D_max, tol, path)

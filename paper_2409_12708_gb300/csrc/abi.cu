@@ -1,17 +1,26 @@
 // abi.cu -- extern "C" entry points declared in include/thc.h.
 #include <cmath>
 #include <string>
+#include <type_traits>
 
-#include "engine_ops.cuh"
+#include "abi_impl.cuh"
 
 #define THC_STR2(x) #x
 #define THC_STR(x) THC_STR2(x)
 
-using thc::Engine;
+using thc::c32;
+using thc::c64;
 using thc::Error;
-using thc::Ops;
-using thc::Profile;
 using thc::Scratch;
+using namespace thc::abi;
+
+// the typed bodies are compiled in inst_*.cu
+THC_ABI_FOR(extern template, double)
+THC_ABI_FOR(extern template, float)
+THC_ABI_FOR(extern template, c64)
+THC_ABI_FOR(extern template, c32)
+THC_ABI_FOR_EXPM(extern template, c64)
+THC_ABI_FOR_EXPM(extern template, c32)
 
 namespace {
 
@@ -50,7 +59,8 @@ void check_opts(const thc_opts* o) {
     if (!o) throw Error(THC_EINVAL, "null options");
     if (o->D_max < 1) throw Error(THC_EINVAL, "D_max must be >= 1");
     if (!(o->tol >= 0.0) || o->tol >= 1.0) throw Error(THC_EINVAL, "tol must be in [0, 1)");
-    if (o->path != THC_PATH_FP64 && o->path != THC_PATH_FP32) throw Error(THC_EINVAL, "bad path");
+    if (o->path != THC_PATH_FP64 && o->path != THC_PATH_FP32 && o->path != THC_PATH_TF32)
+        throw Error(THC_EINVAL, "bad path");
     if (o->D_max > 512) throw Error(THC_EUNSUPPORTED, "D_max above 512 is not supported");
 }
 
@@ -61,181 +71,30 @@ void check_ham(const thc_hamiltonian* H, int L) {
 }
 
 thc_dtype real_dtype(thc_path p) { return p == THC_PATH_FP64 ? THC_F64 : THC_F32; }
+thc_dtype complex_dtype(thc_path p) { return p == THC_PATH_FP64 ? THC_C128 : THC_C64; }  // FP32, TF32: C64
+bool is_complex(thc_dtype d) { return d == THC_C64 || d == THC_C128; }
 
 void check_path_dtype(const thc_mps* m, const thc_opts* o) {
-    if (m->dtype != real_dtype(o->path))
-        throw Error(THC_EINVAL, "MPS dtype does not match the compute path (F64 for FP64, F32 for FP32)");
+    if (m->dtype != real_dtype(o->path) && m->dtype != complex_dtype(o->path))
+        throw Error(THC_EINVAL, "MPS dtype does not match the compute path (F64 or C128 for FP64, F32 or C64 "
+                                "for FP32 and TF32)");
 }
 
-// Shared per-call state: engine, device status word, scratch.
-template <class T>
-struct Call {
-    Engine<T> E;
-    Scratch sc;
-    Ops<T> ops;
-    Call(void* stream, const thc_allocator* a)
-        : E((cudaStream_t)stream, a), sc(E.al), ops(E) {
-        E.dflag = sc.get<int>(1);
-        E.ddbg = sc.get<double>(8);
-        THC_CUDA(cudaMemsetAsync(E.dflag, 0, sizeof(int), E.st));
-        THC_CUDA(cudaMemsetAsync(E.ddbg, 0, 8 * sizeof(double), E.st));
+// Call f with a null pointer of the storage scalar of dtype d (the engine's T).
+template <class F>
+thc_status dispatch(thc_dtype d, F&& f) {
+    switch (d) {
+        case THC_F64: return f((double*)nullptr);
+        case THC_F32: return f((float*)nullptr);
+        case THC_C128: return f((c64*)nullptr);
+        case THC_C64: return f((c32*)nullptr);
     }
-    thc_status finish() {
-        int f = 0;
-        double d[8];
-        THC_CUDA(cudaMemcpyAsync(&f, E.dflag, sizeof(int), cudaMemcpyDeviceToHost, E.st));
-        THC_CUDA(cudaMemcpyAsync(d, E.ddbg, 8 * sizeof(double), cudaMemcpyDeviceToHost, E.st));
-        THC_CUDA(cudaStreamSynchronize(E.st));
-        {
-            unsigned long long c[4];
-            std::memcpy(c, d + 4, sizeof(c));
-            auto& p = thc::profiler();
-            std::lock_guard<std::mutex> g(p.mu);
-            if (p.on) {  // sweep statistics ride along with the profile
-                auto& a = p.acc["jacobi_sweeps_all"];
-                a.first += (long)c[1];
-                a.second += (double)c[0];
-                auto& b = p.acc["jacobi_sweeps_p_ge_128"];
-                b.first += (long)c[3];
-                b.second += (double)c[2];
-            }
-        }
-        if (f & thc::DEV_NONFINITE) return fail(THC_ENONFINITE, "non-finite value met in a decomposition");
-        if (f & thc::DEV_SMALL_NONCONV) return fail(THC_ETIMEOUT, "small eigensolver sweep budget exhausted");
-        if (f & thc::DEV_NONCONVERGED) {
-            // not an error: the projector correction keeps the state exact and the
-            // kept subspace is orthogonal to the rotation threshold of the last
-            // sweep; counted, with the rotations that sweep still applied
-            auto& p = thc::profiler();
-            std::lock_guard<std::mutex> g(p.mu);
-            auto& x = p.acc["jacobi_budget_exhausted"];
-            x.first += 1;
-            x.second = std::max(x.second, d[2]);
-        }
-        return THC_OK;
-    }
-};
-
-std::vector<int> bonds_of(const thc_mps* m) { return std::vector<int>(m->bond, m->bond + m->L + 1); }
-
-std::vector<int> pad_up(const std::vector<int>& a, const std::vector<int>& b) {
-    std::vector<int> r(a.size());
-    for (size_t i = 0; i < a.size(); ++i) r[i] = std::max(a[i], b[i]);
-    return r;
+    throw Error(THC_EINVAL, "bad dtype");
 }
 
-template <class T>
-thc_status apply_H_t(const thc_hamiltonian* H, const thc_mps* psi, const thc_opts* o, thc_mps* out,
-                     const thc_allocator* a, void* stream) {
-    Call<T> c(stream, a);
-    const int L = psi->L;
-    const auto pf = thc::full_profile(L, o->D_max);
-    const auto pin = pad_up(bonds_of(psi), pf);
-    T* psi_d = c.sc.template get<T>((size_t)Profile(pin).size);
-    c.ops.upload(psi, pin, psi_d);
-    T* out_d = c.sc.template get<T>((size_t)Profile(pf).size);
-    c.ops.apply_H(H, psi_d, pin, o, out_d);
-    c.ops.download(out_d, pf, out, psi->dtype);
-    return c.finish();
-}
-
-template <class T>
-thc_status layer_t(const thc_mps* psi, const double* coef, int sigma, int dagger, const thc_opts* o,
-                   thc_mps* out, const thc_allocator* a, void* stream) {
-    Call<T> c(stream, a);
-    c.E.tol_ = o->tol;
-    const auto pin = bonds_of(psi);
-    T* psi_d = c.sc.template get<T>((size_t)Profile(pin).size);
-    c.ops.upload(psi, pin, psi_d);
-    thc::Plan P = thc::make_plan<T>(thc::MODE_LAYER, pin, {}, o->D_max);
-    T* out_d = c.sc.template get<T>((size_t)Profile(P.out).size);
-    std::vector<int> pout;
-    c.ops.layer_apply(psi_d, pin, coef, sigma, dagger, o->D_max, out_d, pout, 1);
-    c.ops.download(out_d, pout, out, psi->dtype);
-    return c.finish();
-}
-
-template <class T>
-thc_status compress_t(const thc_mps* psi, const thc_opts* o, thc_mps* out, const thc_allocator* a,
-                      void* stream) {
-    Call<T> c(stream, a);
-    c.E.tol_ = o->tol;
-    const auto pin = bonds_of(psi);
-    T* psi_d = c.sc.template get<T>((size_t)Profile(pin).size);
-    c.ops.upload(psi, pin, psi_d);
-    thc::Plan P = thc::make_plan<T>(thc::MODE_PLAIN, pin, {}, o->D_max);
-    T* out_d = c.sc.template get<T>((size_t)Profile(P.out).size);
-    std::vector<int> pout;
-    c.ops.plain_compress(psi_d, pin, o->D_max, out_d, pout);
-    c.ops.download(out_d, pout, out, psi->dtype);
-    return c.finish();
-}
-
-template <class T>
-thc_status inner_t(const thc_mps* phi, const thc_mps* psi, double* re, void* stream) {
-    Call<T> c(stream, nullptr);
-    const auto pa = bonds_of(phi), pb = bonds_of(psi);
-    T* a = c.sc.template get<T>((size_t)Profile(pa).size);
-    T* b = c.sc.template get<T>((size_t)Profile(pb).size);
-    c.ops.upload(phi, pa, a);
-    c.ops.upload(psi, pb, b);
-    *re = c.ops.inner1(a, pa, b, pb);
-    return c.finish();
-}
-
-template <class T>
-thc_status add_t(int n, const double* cre, const thc_mps* const* xs, const thc_opts* o, thc_mps* out,
-                 const thc_allocator* a, void* stream) {
-    Call<T> c(stream, a);
-    c.E.tol_ = o->tol;
-    const int L = xs[0]->L;
-    const auto pf = thc::full_profile(L, o->D_max);
-    const long sz = Profile(pf).size;
-    T* buf = c.sc.template get<T>((size_t)n * sz);
-    std::vector<const T*> ptrs(n);
-    for (int i = 0; i < n; ++i) {
-        for (int b = 0; b <= L; ++b)
-            if (xs[i]->bond[b] > pf[b])
-                throw Error(THC_EUNSUPPORTED, "add_compress inputs must have bonds <= min(D_max, 4^b, 4^(L-b))");
-        c.ops.upload(xs[i], pf, buf + (long)i * sz);
-        ptrs[i] = buf + (long)i * sz;
-    }
-    T* out_d = c.sc.template get<T>((size_t)sz);
-    c.ops.add_compress(n, cre, ptrs.data(), pf, o->D_max, out_d);
-    c.ops.download(out_d, pf, out, xs[0]->dtype);
-    return c.finish();
-}
-
-template <class T>
-thc_status lanczos_t(const thc_hamiltonian* H, const thc_mps* psi0, int K, const thc_opts* o,
-                     double* energy, double* ritz, thc_mps* ground, const thc_allocator* a, void* stream) {
-    Call<T> c(stream, a);
-    const int L = psi0->L;
-    const auto pf = thc::full_profile(L, o->D_max);
-    for (int b = 0; b <= L; ++b)
-        if (psi0->bond[b] > pf[b])
-            throw Error(THC_EUNSUPPORTED, "psi0 bonds must be <= min(D_max, 4^b, 4^(L-b))");
-    const long sz = Profile(pf).size;
-    T* p0 = c.sc.template get<T>((size_t)sz);
-    c.ops.upload(psi0, pf, p0);
-    T* vbuf = c.sc.template get<T>((size_t)K * sz);
-    T* wbuf = c.sc.template get<T>((size_t)K * sz);
-    std::vector<double> Ht, S, rz, cre, cim;
-    const int nv = c.ops.krylov_basis(H, p0, pf, K, o, vbuf, wbuf, Ht, S);
-    int rank = 0;
-    c.ops.krylov_small(nv, Ht, S, 0, 0.0, rz, cre, cim, rank);
-    if (rank < 1) throw Error(THC_EBREAKDOWN, "no Krylov vector survived canonical orthogonalisation");
-    *energy = rz[0];
-    if (ritz)
-        for (int i = 0; i < K; ++i) ritz[i] = i < rank ? rz[i] : std::nan("");
-    if (ground) {
-        std::vector<const T*> xs(nv);
-        for (int i = 0; i < nv; ++i) xs[i] = vbuf + (long)i * sz;
-        T* g = c.sc.template get<T>((size_t)sz);
-        c.ops.add_compress(nv, cre.data(), xs.data(), pf, o->D_max, g);
-        c.ops.download(g, pf, ground, psi0->dtype);
-    }
-    return c.finish();
+// complex MPS support the bond dimensions of D_max <= 256
+void check_complex_dmax(thc_dtype d, const thc_opts* o) {
+    if (is_complex(d) && o->D_max > 256) throw Error(THC_EUNSUPPORTED, "complex MPS: D_max above 256 is not supported");
 }
 
 #define THC_GUARD(...)                                                    \
@@ -263,9 +122,12 @@ thc_status thc_apply_H(const thc_hamiltonian* H, const thc_mps* psi, const thc_o
         check_opts(opts);
         check_ham(H, psi->L);
         check_path_dtype(psi, opts);
+        check_complex_dmax(psi->dtype, opts);
         if (!out) throw Error(THC_EINVAL, "null output");
-        if (opts->path == THC_PATH_FP64) return apply_H_t<double>(H, psi, opts, out, alloc, stream);
-        return apply_H_t<float>(H, psi, opts, out, alloc, stream);
+        return dispatch(psi->dtype, [&](auto* tag) {
+            using T = std::remove_pointer_t<decltype(tag)>;
+            return apply_H_t<T>(H, psi, opts, out, alloc, stream);
+        });
     })
 }
 
@@ -275,10 +137,13 @@ thc_status thc_layer_apply(const thc_mps* psi, const double* coef, int sigma, in
         check_mps(psi, "psi");
         check_opts(opts);
         check_path_dtype(psi, opts);
+        check_complex_dmax(psi->dtype, opts);
         if (!coef || !out) throw Error(THC_EINVAL, "null coefficient or output");
         if (sigma != 0 && sigma != 1) throw Error(THC_EINVAL, "sigma must be 0 or 1");
-        if (opts->path == THC_PATH_FP64) return layer_t<double>(psi, coef, sigma, dagger, opts, out, alloc, stream);
-        return layer_t<float>(psi, coef, sigma, dagger, opts, out, alloc, stream);
+        return dispatch(psi->dtype, [&](auto* tag) {
+            using T = std::remove_pointer_t<decltype(tag)>;
+            return layer_t<T>(psi, coef, sigma, dagger, opts, out, alloc, stream);
+        });
     })
 }
 
@@ -288,9 +153,12 @@ thc_status thc_compress(const thc_mps* psi, const thc_opts* opts, thc_mps* out,
         check_mps(psi, "psi");
         check_opts(opts);
         check_path_dtype(psi, opts);
+        check_complex_dmax(psi->dtype, opts);
         if (!out) throw Error(THC_EINVAL, "null output");
-        if (opts->path == THC_PATH_FP64) return compress_t<double>(psi, opts, out, alloc, stream);
-        return compress_t<float>(psi, opts, out, alloc, stream);
+        return dispatch(psi->dtype, [&](auto* tag) {
+            using T = std::remove_pointer_t<decltype(tag)>;
+            return compress_t<T>(psi, opts, out, alloc, stream);
+        });
     })
 }
 
@@ -301,10 +169,10 @@ thc_status mps_inner(const thc_mps* phi, const thc_mps* psi, double* out_re, dou
         if (phi->L != psi->L) throw Error(THC_EINVAL, "L mismatch");
         if (phi->dtype != psi->dtype) throw Error(THC_EINVAL, "dtype mismatch");
         if (!out_re) throw Error(THC_EINVAL, "null output");
-        if (out_im) *out_im = 0.0;
-        if (phi->dtype == THC_F64) return inner_t<double>(phi, psi, out_re, stream);
-        if (phi->dtype == THC_F32) return inner_t<float>(phi, psi, out_re, stream);
-        throw Error(THC_EUNSUPPORTED, "complex MPS are not supported by this build");
+        return dispatch(phi->dtype, [&](auto* tag) {
+            using T = std::remove_pointer_t<decltype(tag)>;
+            return inner_t<T>(phi, psi, out_re, out_im, stream);
+        });
     })
 }
 
@@ -317,12 +185,16 @@ thc_status mps_add_compress(int n, const double* coeff_re, const double* coeff_i
             check_mps(xs[i], "x");
             check_path_dtype(xs[i], opts);
             if (xs[i]->L != xs[0]->L) throw Error(THC_EINVAL, "L mismatch");
+            if (xs[i]->dtype != xs[0]->dtype) throw Error(THC_EINVAL, "dtype mismatch");
         }
-        if (coeff_im)
+        check_complex_dmax(xs[0]->dtype, opts);
+        if (coeff_im && !is_complex(xs[0]->dtype))
             for (int i = 0; i < n; ++i)
-                if (coeff_im[i] != 0.0) throw Error(THC_EUNSUPPORTED, "complex coefficients are not supported");
-        if (opts->path == THC_PATH_FP64) return add_t<double>(n, coeff_re, xs, opts, out, alloc, stream);
-        return add_t<float>(n, coeff_re, xs, opts, out, alloc, stream);
+                if (coeff_im[i] != 0.0) throw Error(THC_EINVAL, "complex coefficients need complex MPS");
+        return dispatch(xs[0]->dtype, [&](auto* tag) {
+            using T = std::remove_pointer_t<decltype(tag)>;
+            return add_t<T>(n, coeff_re, coeff_im, xs, opts, out, alloc, stream);
+        });
     })
 }
 
@@ -334,33 +206,77 @@ thc_status krylov_lanczos_ground(const thc_hamiltonian* H, const thc_mps* psi0, 
         check_opts(opts);
         check_ham(H, psi0->L);
         check_path_dtype(psi0, opts);
+        check_complex_dmax(psi0->dtype, opts);
         if (K < 1 || K > thc::SMALL_MAX) throw Error(THC_EINVAL, "K must be in [1, 64]");
         if (!energy) throw Error(THC_EINVAL, "null energy");
-        if (opts->path == THC_PATH_FP64)
-            return lanczos_t<double>(H, psi0, K, opts, energy, ritz, ground, alloc, stream);
-        return lanczos_t<float>(H, psi0, K, opts, energy, ritz, ground, alloc, stream);
+        return dispatch(psi0->dtype, [&](auto* tag) {
+            using T = std::remove_pointer_t<decltype(tag)>;
+            return lanczos_t<T>(H, psi0, K, opts, energy, ritz, ground, alloc, stream);
+        });
+    })
+}
+
+thc_status krylov_lanczos_restarted(const thc_hamiltonian* H, const thc_mps* psi0, int K, int cycles, int n_lower,
+                                    const thc_mps* const* lower, const thc_opts* opts, double* energies,
+                                    thc_mps* state, const thc_allocator* alloc, void* stream) {
+    THC_GUARD({
+        check_mps(psi0, "psi0");
+        check_opts(opts);
+        check_ham(H, psi0->L);
+        check_path_dtype(psi0, opts);
+        check_complex_dmax(psi0->dtype, opts);
+        if (K < 1 || K > thc::SMALL_MAX) throw Error(THC_EINVAL, "K must be in [1, 64]");
+        if (cycles < 1) throw Error(THC_EINVAL, "cycles must be >= 1");
+        if (n_lower < 0 || (n_lower > 0 && !lower)) throw Error(THC_EINVAL, "bad lower states");
+        if (!energies) throw Error(THC_EINVAL, "null energies");
+        for (int m = 0; m < n_lower; ++m) {
+            check_mps(lower[m], "lower");
+            if (lower[m]->L != psi0->L || lower[m]->dtype != psi0->dtype)
+                throw Error(THC_EINVAL, "lower states must match psi0's L and dtype");
+        }
+        return dispatch(psi0->dtype, [&](auto* tag) {
+            using T = std::remove_pointer_t<decltype(tag)>;
+            return restarted_t<T>(H, psi0, K, cycles, n_lower, lower, opts, energies, state, alloc, stream);
+        });
     })
 }
 
 thc_status krylov_expm_apply(const thc_hamiltonian* H, const thc_mps* psi, double dt, int K,
                              const thc_opts* opts, thc_mps* out, double* lost_norm,
                              const thc_allocator* alloc, void* stream) {
-    (void)H; (void)psi; (void)dt; (void)K; (void)opts; (void)out; (void)lost_norm; (void)alloc; (void)stream;
-    return fail(THC_EUNSUPPORTED, "complex MPS (time evolution) are not supported by this build");
+    THC_GUARD({
+        check_mps(psi, "psi");
+        check_opts(opts);
+        check_ham(H, psi->L);
+        check_path_dtype(psi, opts);
+        check_complex_dmax(complex_dtype(opts->path), opts);
+        if (K < 1 || K > thc::SMALL_MAX) throw Error(THC_EINVAL, "K must be in [1, 64]");
+        if (!out) throw Error(THC_EINVAL, "null output");
+        if (!std::isfinite(dt)) throw Error(THC_EINVAL, "dt must be finite");
+        if (opts->path == THC_PATH_FP64) return expm_t<c64>(H, psi, dt, K, opts, out, lost_norm, alloc, stream);
+        return expm_t<c32>(H, psi, dt, K, opts, out, lost_norm, alloc, stream);
+    })
 }
 
 thc_status thc_kinetic_factors(int L, const double* t, double* lambda, double* u, void* stream) {
     THC_GUARD({
         if (L < 1 || L > thc::SMALL_MAX || !t || !lambda || !u) throw Error(THC_EINVAL, "bad arguments");
-        Engine<double> E((cudaStream_t)stream, nullptr);
-        Scratch sc(E.al);
+        const cudaStream_t st = (cudaStream_t)stream;
+        thc::Alloc al;
+        al.st = st;
+        Scratch sc(al);
         int* flag = sc.get<int>(1);
-        THC_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), E.st));
-        thc::k_kinetic_factors<<<1, 256, thc::KINETIC_SMEM, E.st>>>(L, t, lambda, u, flag);
-        E.check();
+        THC_CUDA(cudaFuncSetAttribute(thc::k_kinetic_factors, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)thc::KINETIC_SMEM));
+        THC_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), st));
+        {
+            THC_LAUNCH("kinetic_eigh", st);
+            thc::k_kinetic_factors<<<1, 256, thc::KINETIC_SMEM, st>>>(L, t, lambda, u, flag);
+        }
+        THC_CUDA(cudaGetLastError());
         int f = 0;
-        THC_CUDA(cudaMemcpyAsync(&f, flag, sizeof(int), cudaMemcpyDeviceToHost, E.st));
-        THC_CUDA(cudaStreamSynchronize(E.st));
+        THC_CUDA(cudaMemcpyAsync(&f, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+        THC_CUDA(cudaStreamSynchronize(st));
         if (f) return fail(THC_ETIMEOUT, "Jacobi sweep budget exhausted");
         return THC_OK;
     })

@@ -78,6 +78,7 @@ enum : int {
     DEV_NONCONVERGED = 1,   // Jacobi sweep budget exhausted
     DEV_NONFINITE = 2,      // NaN/Inf met in a decomposition
     DEV_SMALL_NONCONV = 4,  // small float64 eigensolver sweep budget exhausted
+    DEV_TC_TIMEOUT = 8,     // a tensor-core kernel gave up waiting for its MMAs
 };
 
 }  // namespace thc

@@ -17,14 +17,17 @@
 #include <mutex>
 #include <stdexcept>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/thc.h"
 #include "common.cuh"
 #include "gemm.cuh"
+#include "scalar.cuh"
 #include "jacobi.cuh"
 #include "qr.cuh"
 #include "small.cuh"
+#include "tc_gemm.cuh"
 
 namespace thc {
 
@@ -206,7 +209,7 @@ struct Plan {
 
 template <class T>
 inline void qr_params(int m, int n, int& nb) {
-    nb = sizeof(T) == 8 ? 16 : 32;  // panel width (at most one warp of reflectors)
+    nb = sizeof(T) >= 8 ? 16 : 32;  // panel width (at most one warp of reflectors)
     const size_t budget = 220 * 1024;
     while (nb > 4 && qr_smem_bytes<T>(m, nb, n) > budget) nb /= 2;
     if (qr_smem_bytes<T>(m, nb, n) > budget)
@@ -274,20 +277,20 @@ inline Plan make_plan(int mode, const std::vector<int>& inA, const std::vector<i
 //   b_up = c (x) I2 : |up> -> |0>, |updn> -> |dn>
 //   b_dn = Z (x) c  : |dn> -> |0>, |updn> -> -|up>
 //   creation operators are the transposes.
-__constant__ signed char c_src[4][4] = {
+static __constant__ signed char c_src[4][4] = {
     {2, 3, -1, -1},   // b_up   : n'=0 <- n=2, n'=1 <- n=3
     {1, -1, 3, -1},   // b_dn   : n'=0 <- n=1, n'=2 <- n=3
     {-1, -1, 0, 1},   // b_up^T : n'=2 <- n=0, n'=3 <- n=1
     {-1, 0, -1, 2},   // b_dn^T : n'=1 <- n=0, n'=3 <- n=2
 };
-__constant__ signed char c_sgn[4][4] = {
+static __constant__ signed char c_sgn[4][4] = {
     {1, 1, 0, 0},
     {1, 0, -1, 0},
     {0, 0, 1, 1},
     {0, 1, 0, -1},
 };
 // Jordan-Wigner string on one site, Z (x) Z = (-1)^(n_up + n_dn)
-__constant__ signed char c_par[4] = {1, -1, -1, 1};
+static __constant__ signed char c_par[4] = {1, -1, -1, 1};
 
 // A-operand of the expand+absorb GEMM for site s: row m = (a_row, n'),
 // column q = (b, beta) over the expanded right bond.
@@ -324,13 +327,14 @@ struct ExpandA {
             const int a = (s == 0) ? 0 : ai;
             const int bb = (s == L - 1) ? 1 : bi;
             const T* in = inA + (long)(srcA ? srcA[b] : b) * strideA + offA;
-            if (a == 0 && bb == 0) return T(c_par[np]) * in[((long)alpha * 4 + np) * rA + beta];
+            if (a == 0 && bb == 0) return tscale(in[((long)alpha * 4 + np) * rA + beta], real_t<T>(c_par[np]));
             if (a == 1 && bb == 1) return in[((long)alpha * 4 + np) * rA + beta];
-            if (a == 1 && bb == 0) return T(0);
+            if (a == 1 && bb == 0) return tzero<T>();
             const int o = opsel[b];
             const int n = c_src[o][np];
-            if (n < 0) return T(0);
-            return coef[(long)b * coef_ld + s] * T(c_sgn[o][np]) * in[((long)alpha * 4 + n) * rA + beta];
+            if (n < 0) return tzero<T>();
+            return coef[(long)b * coef_ld + s] *
+                   tscale(in[((long)alpha * 4 + n) * rA + beta], real_t<T>(c_sgn[o][np]));
         }
         if (mode == MODE_PLAIN) {
             const T* in = inA + (long)(srcA ? srcA[b] : b) * strideA + offA;
@@ -341,7 +345,7 @@ struct ExpandA {
         if (s == 0) which = bi;
         else if (s == L - 1) which = ai;
         else which = (ai == bi) ? ai : -1;
-        if (which < 0) return T(0);
+        if (which < 0) return tzero<T>();
         if (which == 0) {
             const T* in = inA + (long)(srcA ? srcA[b] : b) * strideA + offA;
             const T v = in[((long)alpha * 4 + np) * rA + beta];
@@ -359,7 +363,7 @@ struct RowMajorB {  // B(k, n) = base_b[k*ld + n]; identity 1x1 when base is nul
     long stride;
     int ld;
     __device__ __forceinline__ T operator()(int b, int k, int n) const {
-        if (!base) return T(1);
+        if (!base) return tone<T>();
         return base[(long)b * stride + (long)k * ld + n];
     }
 };
@@ -375,12 +379,12 @@ struct RowMajorA {  // A(m, k) = base_b[m*ld + k]
 };
 
 template <class T>
-struct TransB {  // B(k, n) = base_b[n*ld + k]
+struct TransB {  // B(k, n) = conj(base_b[n*ld + k]) (the conjugate transpose; real: transpose)
     const T* base;
     long stride;
     int ld;
     __device__ __forceinline__ T operator()(int b, int k, int n) const {
-        return base[(long)b * stride + (long)n * ld + k];
+        return tconj(base[(long)b * stride + (long)n * ld + k]);
     }
 };
 
@@ -391,7 +395,7 @@ struct StoreRM {  // C(m, n) -> base_b[m*ld + n]
     int ld;
     template <class A>
     __device__ __forceinline__ void operator()(int b, int m, int n, A v) const {
-        base[(long)b * stride + (long)m * ld + n] = T(v);
+        base[(long)b * stride + (long)m * ld + n] = cvt<T>(v);
     }
 };
 
@@ -404,14 +408,14 @@ struct StoreRMandCM {  // row-major C and a column-major copy (for the QR of C)
     int M, N;
     template <class A>
     __device__ __forceinline__ void operator()(int b, int m, int n, A v) const {
-        rm[(long)b * srm + (long)m * N + n] = T(v);
-        if (cm) cm[(long)b * scm + (long)n * M + m] = T(v);
+        rm[(long)b * srm + (long)m * N + n] = cvt<T>(v);
+        if (cm) cm[(long)b * scm + (long)n * M + m] = cvt<T>(v);
     }
 };
 
 template <class T>
 struct IdentA {  // the 1x1 identity (M_{-1} of the SVD sweep)
-    __device__ __forceinline__ T operator()(int, int, int) const { return T(1); }
+    __device__ __forceinline__ T operator()(int, int, int) const { return tone<T>(); }
 };
 
 // C of the SVD sweep, written row-major [(alpha, n') x j] and, when a QR of C
@@ -425,44 +429,33 @@ struct StoreC {
     int mC, nC, NG;
     template <class A>
     __device__ __forceinline__ void operator()(int b, int r, int col, A v) const {
-        rm[(long)b * srm + (long)r * NG + col] = T(v);
+        rm[(long)b * srm + (long)r * NG + col] = cvt<T>(v);
         if (cm) {
             const int row = r * 4 + col / nC, j = col % nC;
-            cm[(long)b * scm + (long)j * mC + row] = T(v);
+            cm[(long)b * scm + (long)j * mC + row] = cvt<T>(v);
         }
-    }
-};
-
-// site-tensor batch stored with per-term pointers (for user MPS / inner products)
-template <class T>
-struct PtrRM {
-    const T* const* ptrs;  // per-term site pointer
-    int ld;
-    bool cj;
-    __device__ __forceinline__ double operator()(int b, int m, int k) const {
-        return double(ptrs[b][(long)m * ld + k]);
     }
 };
 
 // ----------------------------------------------------------------------------
 // small kernels
 // ----------------------------------------------------------------------------
-template <class T>
-__global__ void k_copy_pad(T* dst, int dl, int dr, const T* src, int sl, int sr) {
-    // dst [dl,4,dr] <- src [sl,4,sr] zero-padded (dl>=sl, dr>=sr)
+template <class T, class S>
+__global__ void k_copy_pad(T* dst, int dl, int dr, const S* src, int sl, int sr) {
+    // dst [dl,4,dr] <- src [sl,4,sr] zero-padded (dl>=sl, dr>=sr), converted to T
     const long n = (long)dl * 4 * dr;
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
         const int r = (int)(i % dr);
         const int np = (int)((i / dr) % 4);
         const int l = (int)(i / (4L * dr));
-        dst[i] = (l < sl && r < sr) ? src[((long)l * 4 + np) * sr + r] : T(0);
+        dst[i] = (l < sl && r < sr) ? cvt<T>(src[((long)l * 4 + np) * sr + r]) : tzero<T>();
     }
 }
 
 template <class D, class S>
 __global__ void k_convert(D* dst, const S* src, long n) {
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-        dst[i] = D(src[i]);
+        dst[i] = cvt<D>(src[i]);
 }
 
 template <class T>
@@ -518,8 +511,8 @@ __global__ void k_term_coefs(int stage, long t0, int B, int L, int N, const doub
     }
     for (int s = threadIdx.x; s < L; s += blockDim.x) {
         const double c = kinetic ? u[(long)s * L + col] : chi[(long)s * N + col];
-        coef1[(long)b * L + s] = T(scale * c);
-        coef2[(long)b * L + s] = T(c);
+        coef1[(long)b * L + s] = cvt<T>(scale * c);
+        coef2[(long)b * L + s] = cvt<T>(c);
     }
     if (threadIdx.x == 0) {
         op1[b] = sig;        // annihilation
@@ -532,8 +525,8 @@ template <class T>
 __global__ void k_pair_coefs(T* coef, int B, const T* cA, const T* cB) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b < B) {
-        coef[2 * b] = cA ? cA[b] : T(1);
-        coef[2 * b + 1] = cB ? cB[b] : T(1);
+        coef[2 * b] = cA ? cA[b] : tone<T>();
+        coef[2 * b + 1] = cB ? cB[b] : tone<T>();
     }
 }
 

@@ -5,7 +5,7 @@
 
 namespace thc {
 
-__global__ void k_pair_src(int* a, int* b, int B, int start) {
+static __global__ void k_pair_src(int* a, int* b, int B, int start) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < B) {
         a[i] = start + 2 * i;
@@ -73,12 +73,36 @@ struct Engine {
         opt_in(k_jacobi_select<T, 4>, big);
         opt_in(k_jacobi_select<T, 8>, big);
         opt_in(k_jacobi_select<T, 16>, big);
-        opt_in(k_jacobi_select<T, 32>, big);
+        if constexpr (!is_complex_v<T>) opt_in(k_jacobi_select<T, 32>, big);
         opt_in(k_kinetic_factors, (int)KINETIC_SMEM);
         opt_in(k_krylov_small, (int)KRYLOV_SMEM);
+        opt_in(k_krylov_small_c, (int)KRYLOV_SMEM_C);
     }
 
     void check() { THC_CUDA(cudaGetLastError()); }
+
+    bool tc = false;  // TF32 path: float32 contractions on the tensor cores (3xTF32)
+
+    // Batched GEMM of the compression: the tensor-core kernel on the TF32 path
+    // (float32 storage, output tiles at least 64 x 64), else the SIMT kernels.
+    template <class LA, class LB, class SC>
+    void gemm(int batch, int M, int N, int K, const LA& la, const LB& lb, const SC& sc) {
+        if constexpr (std::is_same<T, float>::value) {
+            if (tc && batch > 0 && M >= 64 && N >= 64 && K >= 1) {
+                static bool attr = false;  // one opt-in per instantiation
+                if (!attr) {
+                    THC_CUDA(cudaFuncSetAttribute(k_gemm_tc<LA, LB, SC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  tc::SMEM));
+                    attr = true;
+                }
+                dim3 grid(ceil_div(N, tc::BN), ceil_div(M, tc::BM), batch);
+                k_gemm_tc<LA, LB, SC><<<grid, tc::THREADS, tc::SMEM, st>>>(M, N, K, la, lb, sc, dflag);
+                THC_CUDA(cudaGetLastError());
+                return;
+            }
+        }
+        THC_CUDA(launch_gemm<T>(batch, M, N, K, la, lb, sc, st));
+    }
 
     // ---------------------------------------------------------------- work
     void alloc_work(Scratch& sc, Work<T>& w, int B, const std::vector<const Plan*>& plans) {
@@ -177,7 +201,7 @@ struct Engine {
             StoreRM<T> sto{w.wide + P.woff[s], w.sWide, Ng};
             {
                 THC_LAUNCH("gemm_expand_absorb", st);
-                THC_CUDA(launch_gemm<T>(B, Mg, Ng, Kg, ex, bop, sto, st));
+                gemm(B, Mg, Ng, Kg, ex, bop, sto);
             }
             if (s >= 1) {
                 QRJob<T> job;
@@ -209,11 +233,11 @@ struct Engine {
             RowMajorB<T> qop{w.wide + P.woff[s], w.sWide, 4 * n};
             if (s == 0) {
                 THC_LAUNCH("gemm_center", st);
-                THC_CUDA(launch_gemm<T>(B, P.out[0], 4 * n, 1, IdentA<T>{}, qop, sto, st));
+                gemm(B, P.out[0], 4 * n, 1, IdentA<T>{}, qop, sto);
             } else {
                 RowMajorA<T> mop{w.M[(s - 1) & 1], w.sV, P.k[s]};
                 THC_LAUNCH("gemm_center", st);
-                THC_CUDA(launch_gemm<T>(B, P.out[s], 4 * n, P.k[s], mop, qop, sto, st));
+                gemm(B, P.out[s], 4 * n, P.k[s], mop, qop, sto);
             }
             int p = std::min(m, n);
             const int* colmap = nullptr;
@@ -252,7 +276,7 @@ struct Engine {
             StoreRM<T> uo{out + pO.off[s], out_stride, kout};
             {
                 THC_LAUNCH("gemm_u", st);
-                THC_CUDA(launch_gemm<T>(B, m, kout, n, cop, vop, uo, st));
+                gemm(B, m, kout, n, cop, vop, uo);
             }
             // normalise U's columns, then M = diag(nu) (I - F') V with F = V V^T
             {
@@ -263,13 +287,13 @@ struct Engine {
             check();
             {
                 THC_LAUNCH("svd_finalize", st);
-                THC_CUDA(launch_gemm<T>(B, kout, kout, n, RowMajorA<T>{w.V, w.sV, n}, TransB<T>{w.V, w.sV, n},
-                                        StoreRM<T>{w.F, w.sF, kout}, st));
+                gemm(B, kout, kout, n, RowMajorA<T>{w.V, w.sV, n}, TransB<T>{w.V, w.sV, n},
+                                        StoreRM<T>{w.F, w.sF, kout});
             }
             {
                 THC_LAUNCH("svd_finalize", st);
-                THC_CUDA(launch_gemm<T>(B, kout, n, kout, CorrA<T>{w.F, w.sF, w.nu, w.sSv, kout},
-                                        RowMajorB<T>{w.V, w.sV, n}, StoreRM<T>{w.M[s & 1], w.sV, n}, st));
+                gemm(B, kout, n, kout, CorrA<T>{w.F, w.sF, w.nu, w.sSv, kout},
+                                        RowMajorB<T>{w.V, w.sV, n}, StoreRM<T>{w.M[s & 1], w.sV, n});
             }
         }
         // ---- last site: M_{L-2} Q_{L-1}
@@ -279,13 +303,13 @@ struct Engine {
             RowMajorB<T> qop{w.wide + P.woff[s], w.sWide, 4 * P.k[s + 1]};
             StoreRM<T> so{out + pO.off[s], out_stride, 4 * P.k[s + 1]};
             THC_LAUNCH("gemm_center", st);
-            THC_CUDA(launch_gemm<T>(B, P.out[s], 4 * P.k[s + 1], P.k[s], mop, qop, so, st));
+            gemm(B, P.out[s], 4 * P.k[s + 1], P.k[s], mop, qop, so);
         }
     }
 
     // rotation threshold on the row cosine: a multiple of the rounding error of
     // the warp dot product (NPL sequential terms per lane + 5 butterfly levels)
-    double rot_tol(int n) const { return 8.0 * (ceil_div(std::max(n, 1), 32) + 6) * Real<T>::eps; }
+    double rot_tol(int n) const { return 8.0 * (ceil_div(std::max(n, 1), 32) + 6) * Real<real_t<T>>::eps; }
     double tol_ = 0.0;
 
     void jacobi_select(int B, int p, int n, int kout, Work<T>& w, const int* colmap) {
@@ -316,8 +340,12 @@ struct Engine {
         if (n <= 128) k_jacobi_select<T, 4><<<B, JacobiCfg<T, 4>::threads, smem, st>>>(j);
         else if (n <= 256) k_jacobi_select<T, 8><<<B, JacobiCfg<T, 8>::threads, smem, st>>>(j);
         else if (n <= 512) k_jacobi_select<T, 16><<<B, JacobiCfg<T, 16>::threads, smem, st>>>(j);
-        else if (n <= 1024) k_jacobi_select<T, 32><<<B, JacobiCfg<T, 32>::threads, smem, st>>>(j);
-        else throw Error(THC_EUNSUPPORTED, "bond dimension above 512 is not supported");
+        else if constexpr (!is_complex_v<T>) {
+            if (n <= 1024) k_jacobi_select<T, 32><<<B, JacobiCfg<T, 32>::threads, smem, st>>>(j);
+            else throw Error(THC_EUNSUPPORTED, "bond dimension above 512 is not supported");
+        } else {
+            throw Error(THC_EUNSUPPORTED, "complex MPS: bond dimension above 256 is not supported");
+        }
         check();
     }
 

@@ -8,11 +8,14 @@
 namespace thc {
 
 // ---------------------------------------------------------------- inner product functors
-struct EA {  // E(m, k), float64 row-major
-    const double* E;
+// Transfer matrices are accumulated in Acc = Wide<T>: float64, or complex
+// float64 for complex MPS.
+template <class Acc>
+struct EA {  // E(m, k), row-major
+    const Acc* E;
     long sE;
     int ld;
-    __device__ __forceinline__ double operator()(int b, int m, int k) const {
+    __device__ __forceinline__ Acc operator()(int b, int m, int k) const {
         return E[(long)b * sE + (long)m * ld + k];
     }
 };
@@ -21,40 +24,51 @@ struct SiteB {  // B(k, n) = site[k*ld + n] of term b
     const T* base;
     long stride;
     int ld;
-    __device__ __forceinline__ double operator()(int b, int k, int n) const {
-        return double(base[(long)b * stride + (long)k * ld + n]);
+    __device__ __forceinline__ typename Wide<T>::type operator()(int b, int k, int n) const {
+        return cvt<typename Wide<T>::type>(base[(long)b * stride + (long)k * ld + n]);
     }
 };
 template <class T>
-struct SiteAT {  // A(m, k) = site[k*ld + m] (transposed access; real: conj is identity)
+struct SiteAT {  // A(m, k) = conj(site[k*ld + m]) (transposed access, conjugated: <phi| side)
     const T* base;
     long stride;
     int ld;
-    __device__ __forceinline__ double operator()(int b, int m, int k) const {
-        return double(base[(long)b * stride + (long)k * ld + m]);
+    __device__ __forceinline__ typename Wide<T>::type operator()(int b, int m, int k) const {
+        return cvt<typename Wide<T>::type>(tconj(base[(long)b * stride + (long)k * ld + m]));
     }
 };
+template <class Acc>
 struct StoreD {
-    double* base;
+    Acc* base;
     long stride;
     int ld;
-    __device__ __forceinline__ void operator()(int b, int m, int n, double v) const {
+    __device__ __forceinline__ void operator()(int b, int m, int n, Acc v) const {
         base[(long)b * stride + (long)m * ld + n] = v;
     }
 };
 
-__global__ void k_set_one(double* E, long stride, int B) {
+template <class Acc>
+__global__ void k_set_one(Acc* E, long stride, int B) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b < B) E[(long)b * stride] = 1.0;
+    if (b < B) E[(long)b * stride] = tone<Acc>();
 }
-__global__ void k_gather_scalar(const double* E, long stride, int B, double* out) {
+template <class Acc>
+__global__ void k_gather_scalar(const Acc* E, long stride, int B, Acc* out) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b < B) out[b] = E[(long)b * stride];
 }
+// x <- c x with a float64 (complex float64) coefficient
 template <class T>
-__global__ void k_scale(T* x, long n, double c) {
+__global__ void k_scale(T* x, long n, typename Wide<T>::type c) {
+    using Acc = typename Wide<T>::type;
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-        x[i] = T(double(x[i]) * c);
+        x[i] = cvt<T>(cvt<Acc>(x[i]) * c);
+}
+
+static __global__ void k_set_int(int* p, int v) { *p = v; }
+
+static __global__ void k_pack_complex(c64* out, const double* re, const double* im, int n) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) out[i] = c64{re[i], im[i]};
 }
 
 // A device MPS in the engine's contiguous layout (one term).
@@ -66,19 +80,32 @@ struct DevMps {
 
 template <class T>
 struct Ops {
+    using Acc = typename Wide<T>::type;  // float64 accumulator (complex for complex T)
     Engine<T>& E;
     explicit Ops(Engine<T>& e) : E(e) {}
     cudaStream_t st() const { return E.st; }
 
     // ------------------------------------------------------------- transfers
+    // copy (zero-padded to prof) a caller's MPS; a real MPS given to a complex
+    // engine is converted on the way
     void upload(const thc_mps* m, const std::vector<int>& prof, T* dst) {
         Profile p(prof);
+        const bool widen = is_complex_v<T> && (m->dtype == THC_F64 || m->dtype == THC_F32);
         for (int s = 0; s < m->L; ++s) {
             const long n = p.site_size(s);
-            const int blocks = (int)std::min<long>(ceil_div((int)std::min<long>(n, 1L << 30), 256), 4096);
+            const int blocks = std::max(1, (int)std::min<long>(ceil_div((int)std::min<long>(n, 1L << 30), 256), 4096));
             THC_LAUNCH("copy", st());
-            k_copy_pad<T><<<std::max(blocks, 1), 256, 0, st()>>>(dst + p.off[s], prof[s], prof[s + 1],
-                                                                  (const T*)m->site[s], m->bond[s], m->bond[s + 1]);
+            if constexpr (is_complex_v<T>) {
+                if (widen) {
+                    k_copy_pad<T, real_t<T>><<<blocks, 256, 0, st()>>>(dst + p.off[s], prof[s], prof[s + 1],
+                                                                         (const real_t<T>*)m->site[s], m->bond[s],
+                                                                         m->bond[s + 1]);
+                    E.check();
+                    continue;
+                }
+            }
+            k_copy_pad<T, T><<<blocks, 256, 0, st()>>>(dst + p.off[s], prof[s], prof[s + 1], (const T*)m->site[s],
+                                                       m->bond[s], m->bond[s + 1]);
             E.check();
         }
     }
@@ -99,7 +126,7 @@ struct Ops {
     // --------------------------------------------------------- inner products
     // <phi_b|psi_b> for B pairs stored strided (phi: base + b*sphi, psi: base + b*spsi).
     void inner_batched(int B, const T* phi, long sphi, const std::vector<int>& pp, const T* psi,
-                       long spsi, const std::vector<int>& pq, double* out_dev) {
+                       long spsi, const std::vector<int>& pq, Acc* out_dev) {
         Profile a(pp), c(pq);
         const int L = a.L;
         int ma = 1, mb = 1;
@@ -107,11 +134,11 @@ struct Ops {
         for (int x : pq) mb = std::max(mb, x);
         Scratch sc(E.al);
         const long sE = (long)ma * mb, sF = (long)ma * 4 * mb;
-        double* Eb = sc.get<double>((size_t)B * sE);
-        double* Fb = sc.get<double>((size_t)B * sF);
+        Acc* Eb = sc.get<Acc>((size_t)B * sE);
+        Acc* Fb = sc.get<Acc>((size_t)B * sF);
         {
             THC_LAUNCH("setup", st());
-            k_set_one<<<ceil_div(B, 128), 128, 0, st()>>>(Eb, sE, B);
+            k_set_one<Acc><<<ceil_div(B, 128), 128, 0, st()>>>(Eb, sE, B);
         }
         E.check();
         for (int s = 0; s < L; ++s) {
@@ -119,29 +146,29 @@ struct Ops {
             // F = E B_s  : [al x bl] x [bl x 4 br]
             {
             THC_LAUNCH("gemm_inner", st());
-            THC_CUDA(launch_gemm<double>(B, al, 4 * br, bl, EA{Eb, sE, bl},
-                                         SiteB<T>{psi + c.off[s], spsi, 4 * br}, StoreD{Fb, sF, 4 * br}, st()));
+            THC_CUDA(launch_gemm<Acc>(B, al, 4 * br, bl, EA<Acc>{Eb, sE, bl},
+                                      SiteB<T>{psi + c.off[s], spsi, 4 * br}, StoreD<Acc>{Fb, sF, 4 * br}, st()));
             }
             // E' = A_s^T F : [(al,4) x ar]^T x [(al,4) x br]
             {
             THC_LAUNCH("gemm_inner", st());
-            THC_CUDA(launch_gemm<double>(B, ar, br, 4 * al, SiteAT<T>{phi + a.off[s], sphi, ar},
-                                         EA{Fb, sF, br}, StoreD{Eb, sE, br}, st()));
+            THC_CUDA(launch_gemm<Acc>(B, ar, br, 4 * al, SiteAT<T>{phi + a.off[s], sphi, ar},
+                                      EA<Acc>{Fb, sF, br}, StoreD<Acc>{Eb, sE, br}, st()));
             }
         }
         {
             THC_LAUNCH("setup", st());
-            k_gather_scalar<<<ceil_div(B, 128), 128, 0, st()>>>(Eb, sE, B, out_dev);
+            k_gather_scalar<Acc><<<ceil_div(B, 128), 128, 0, st()>>>(Eb, sE, B, out_dev);
         }
         E.check();
     }
 
-    double inner1(const T* phi, const std::vector<int>& pp, const T* psi, const std::vector<int>& pq) {
+    Acc inner1(const T* phi, const std::vector<int>& pp, const T* psi, const std::vector<int>& pq) {
         Scratch sc(E.al);
-        double* d = sc.get<double>(1);
+        Acc* d = sc.get<Acc>(1);
         inner_batched(1, phi, 0, pp, psi, 0, pq, d);
-        double h = 0;
-        THC_CUDA(cudaMemcpyAsync(&h, d, sizeof(double), cudaMemcpyDeviceToHost, st()));
+        Acc h = tzero<Acc>();
+        THC_CUDA(cudaMemcpyAsync(&h, d, sizeof(Acc), cudaMemcpyDeviceToHost, st()));
         THC_CUDA(cudaStreamSynchronize(st()));
         return h;
     }
@@ -159,7 +186,11 @@ struct Ops {
             k_convert<T, double><<<1, 64, 0, st()>>>(w.coef1, coef_dev, L);
         }
         const int op = sigma + 2 * (dagger ? 1 : 0);
-        THC_CUDA(cudaMemcpyAsync(w.op1, &op, sizeof(int), cudaMemcpyHostToDevice, st()));
+        {
+            THC_LAUNCH("setup", st());
+            k_set_int<<<1, 1, 0, st()>>>(w.op1, op);
+        }
+        E.check();
         ExpandA<T> ex{};
         ex.mode = MODE_LAYER;
         ex.inA = psi;
@@ -169,7 +200,6 @@ struct Ops {
         ex.opsel = w.op1;
         E.compress(P, 1, ex, out, 0, w);
         pout = P.out;
-        THC_CUDA(cudaStreamSynchronize(st()));  // host op value must outlive the copy
     }
 
     void plain_compress(const T* psi, const std::vector<int>& pin, int D, T* out, std::vector<int>& pout) {
@@ -314,7 +344,7 @@ struct Ops {
 
     // ------------------------------------------------------ add and compress
     // sum_i c_i x_i (all with profile pf, the full profile of D) by the pairwise reduction.
-    void add_compress(int n, const double* c, const T* const* xs, const std::vector<int>& pf, int D,
+    void add_compress(int n, const Acc* c, const T* const* xs, const std::vector<int>& pf, int D,
                       T* out) {
         Profile P(pf);
         Scratch sc(E.al);
@@ -336,91 +366,121 @@ struct Ops {
 
     // ------------------------------------------------------------- Lanczos
     // Returns the number of Krylov vectors; Ht, S (n x n host, row-major).
+    // lower: optional orthonormal states (profile pf) the start vector and
+    // every Krylov vector are orthogonalised against, in the same Gram-Schmidt
+    // sum (excited states).
     int krylov_basis(const thc_hamiltonian* H, const T* psi0, const std::vector<int>& pf, int K,
-                     const thc_opts* o, T* vbuf, T* wbuf, std::vector<double>& Ht,
-                     std::vector<double>& S) {
+                     const thc_opts* o, T* vbuf, T* wbuf, std::vector<Acc>& Ht,
+                     std::vector<Acc>& S, const std::vector<const T*>& lower = {}) {
         Profile P(pf);
         const long sz = P.size;
-        THC_CUDA(cudaMemcpyAsync(vbuf, psi0, sz * sizeof(T), cudaMemcpyDeviceToDevice, st()));
-        const double n0 = std::sqrt(std::fabs(inner1(vbuf, pf, vbuf, pf)));
+        const int nl = (int)lower.size();
+        if (nl > 0) {
+            // v_0 = psi0 - sum_m <phi_m|psi0> phi_m
+            std::vector<const T*> xs{psi0};
+            std::vector<Acc> cs{tone<Acc>()};
+            for (int m = 0; m < nl; ++m) {
+                xs.push_back(lower[m]);
+                cs.push_back(tzero<Acc>() - inner1(lower[m], pf, psi0, pf));
+            }
+            add_compress((int)xs.size(), cs.data(), xs.data(), pf, o->D_max, vbuf);
+        } else {
+            THC_CUDA(cudaMemcpyAsync(vbuf, psi0, sz * sizeof(T), cudaMemcpyDeviceToDevice, st()));
+        }
+        const double n0 = std::sqrt(std::fabs(treal_part(inner1(vbuf, pf, vbuf, pf))));
         if (!(n0 > 0.0)) throw Error(THC_EBREAKDOWN, "zero initial vector");
         {
             THC_LAUNCH("scale", st());
-            k_scale<T><<<64, 256, 0, st()>>>(vbuf + P.off[P.L - 1], P.site_size(P.L - 1), 1.0 / n0);
+            k_scale<T><<<64, 256, 0, st()>>>(vbuf + P.off[P.L - 1], P.site_size(P.L - 1), cvt<Acc>(1.0 / n0));
         }
         E.check();
         int nv = 1;
         Scratch sc(E.al);
-        double* hd = sc.get<double>((size_t)K + 1);
+        Acc* hd = sc.get<Acc>((size_t)K + 1);
         for (int k = 0; k < K; ++k) {
             apply_H(H, vbuf + k * sz, pf, o, wbuf + k * sz);
             if (k == K - 1) break;
             inner_batched(k + 1, vbuf, sz, pf, wbuf + k * sz, 0, pf, hd);
-            std::vector<double> h(k + 1);
-            THC_CUDA(cudaMemcpyAsync(h.data(), hd, (k + 1) * sizeof(double), cudaMemcpyDeviceToHost, st()));
+            std::vector<Acc> h(k + 1);
+            THC_CUDA(cudaMemcpyAsync(h.data(), hd, (k + 1) * sizeof(Acc), cudaMemcpyDeviceToHost, st()));
             THC_CUDA(cudaStreamSynchronize(st()));
             std::vector<const T*> xs;
-            std::vector<double> cs;
+            std::vector<Acc> cs;
             xs.push_back(wbuf + k * sz);
-            cs.push_back(1.0);
+            cs.push_back(tone<Acc>());
             for (int j = 0; j <= k; ++j) {
                 xs.push_back(vbuf + j * sz);
-                cs.push_back(-h[j]);
+                cs.push_back(tzero<Acc>() - h[j]);
+            }
+            for (int m = 0; m < nl; ++m) {
+                xs.push_back(lower[m]);
+                cs.push_back(tzero<Acc>() - inner1(lower[m], pf, wbuf + k * sz, pf));
             }
             T* r = vbuf + (k + 1) * sz;
             add_compress((int)xs.size(), cs.data(), xs.data(), pf, o->D_max, r);
-            const double nr = std::sqrt(std::fabs(inner1(r, pf, r, pf)));
-            const double nw = std::sqrt(std::fabs(inner1(wbuf + k * sz, pf, wbuf + k * sz, pf)));
+            const double nr = std::sqrt(std::fabs(treal_part(inner1(r, pf, r, pf))));
+            const double nw = std::sqrt(std::fabs(treal_part(inner1(wbuf + k * sz, pf, wbuf + k * sz, pf))));
             if (!(nr >= 1e-8 * nw)) break;
             {
                 THC_LAUNCH("scale", st());
-                k_scale<T><<<64, 256, 0, st()>>>(r + P.off[P.L - 1], P.site_size(P.L - 1), 1.0 / nr);
+                k_scale<T><<<64, 256, 0, st()>>>(r + P.off[P.L - 1], P.site_size(P.L - 1), cvt<Acc>(1.0 / nr));
             }
             E.check();
             nv = k + 2;
         }
-        Ht.assign((size_t)nv * nv, 0.0);
-        S.assign((size_t)nv * nv, 0.0);
-        double* col = sc.get<double>((size_t)nv);
-        std::vector<double> tmp(nv);
+        Ht.assign((size_t)nv * nv, tzero<Acc>());
+        S.assign((size_t)nv * nv, tzero<Acc>());
+        Acc* col = sc.get<Acc>((size_t)nv);
+        std::vector<Acc> tmp(nv);
         for (int k = 0; k < nv; ++k) {
             inner_batched(nv, vbuf, sz, pf, wbuf + k * sz, 0, pf, col);
-            THC_CUDA(cudaMemcpyAsync(tmp.data(), col, nv * sizeof(double), cudaMemcpyDeviceToHost, st()));
+            THC_CUDA(cudaMemcpyAsync(tmp.data(), col, nv * sizeof(Acc), cudaMemcpyDeviceToHost, st()));
             THC_CUDA(cudaStreamSynchronize(st()));
             for (int j = 0; j < nv; ++j) Ht[(size_t)j * nv + k] = tmp[j];
             inner_batched(nv, vbuf, sz, pf, vbuf + k * sz, 0, pf, col);
-            THC_CUDA(cudaMemcpyAsync(tmp.data(), col, nv * sizeof(double), cudaMemcpyDeviceToHost, st()));
+            THC_CUDA(cudaMemcpyAsync(tmp.data(), col, nv * sizeof(Acc), cudaMemcpyDeviceToHost, st()));
             THC_CUDA(cudaStreamSynchronize(st()));
             for (int j = 0; j < nv; ++j) S[(size_t)j * nv + k] = tmp[j];
         }
         return nv;
     }
 
-    // projected problem on the device (float64 single-CTA kernel)
-    void krylov_small(int nv, const std::vector<double>& Ht, const std::vector<double>& S, int mode,
-                      double dt, std::vector<double>& ritz, std::vector<double>& cre,
-                      std::vector<double>& cim, int& rank) {
+    // projected problem on the device (float64 single-CTA kernel; the complex
+    // Hermitian kernel for complex Krylov vectors).  Outputs: ritz values
+    // (mode 0), coefficients of the result on the v_i, the kept rank.
+    void krylov_small(int nv, const std::vector<Acc>& Ht, const std::vector<Acc>& S, int mode, double dt,
+                      std::vector<double>& ritz, std::vector<c64>& coef, int& rank) {
         if (nv > SMALL_MAX) throw Error(THC_EINVAL, "Krylov dimension above 64");
         Scratch sc(E.al);
-        double* d = sc.get<double>((size_t)2 * nv * nv + 3 * nv);
+        Acc* d = sc.get<Acc>((size_t)2 * nv * nv);
+        double* rz = sc.get<double>((size_t)nv);
+        c64* cf = sc.get<c64>((size_t)nv);
         int* info = sc.get<int>(2);
-        THC_CUDA(cudaMemcpyAsync(d, Ht.data(), nv * nv * sizeof(double), cudaMemcpyHostToDevice, st()));
-        THC_CUDA(cudaMemcpyAsync(d + nv * nv, S.data(), nv * nv * sizeof(double), cudaMemcpyHostToDevice, st()));
-        double* rz = d + 2 * nv * nv;
-        double* cr = rz + nv;
-        double* ci = cr + nv;
-        {
+        THC_CUDA(cudaMemcpyAsync(d, Ht.data(), nv * nv * sizeof(Acc), cudaMemcpyHostToDevice, st()));
+        THC_CUDA(cudaMemcpyAsync(d + nv * nv, S.data(), nv * nv * sizeof(Acc), cudaMemcpyHostToDevice, st()));
+        if constexpr (is_complex_v<T>) {
             THC_LAUNCH("krylov_small", st());
-            k_krylov_small<<<1, 256, KRYLOV_SMEM, st()>>>(nv, d, d + nv * nv, mode, dt, 1e-12, rz, cr, ci, info);
+            k_krylov_small_c<<<1, 256, KRYLOV_SMEM_C, st()>>>(nv, d, d + nv * nv, mode, dt, 1e-12, rz, cf, info);
+        } else {
+            double* cr = sc.get<double>((size_t)2 * nv);
+            THC_CUDA(cudaMemsetAsync(cr, 0, 2 * nv * sizeof(double), st()));  // mode 0 writes no imaginary part
+            {
+                THC_LAUNCH("krylov_small", st());
+                k_krylov_small<<<1, 256, KRYLOV_SMEM, st()>>>(nv, d, d + nv * nv, mode, dt, 1e-12, rz, cr, cr + nv,
+                                                              info);
+            }
+            E.check();
+            {
+                THC_LAUNCH("setup", st());
+                k_pack_complex<<<1, 64, 0, st()>>>(cf, cr, cr + nv, nv);
+            }
         }
         E.check();
         ritz.resize(nv);
-        cre.resize(nv);
-        cim.resize(nv);
+        coef.resize(nv);
         int inf[2];
         THC_CUDA(cudaMemcpyAsync(ritz.data(), rz, nv * sizeof(double), cudaMemcpyDeviceToHost, st()));
-        THC_CUDA(cudaMemcpyAsync(cre.data(), cr, nv * sizeof(double), cudaMemcpyDeviceToHost, st()));
-        THC_CUDA(cudaMemcpyAsync(cim.data(), ci, nv * sizeof(double), cudaMemcpyDeviceToHost, st()));
+        THC_CUDA(cudaMemcpyAsync(coef.data(), cf, nv * sizeof(c64), cudaMemcpyDeviceToHost, st()));
         THC_CUDA(cudaMemcpyAsync(inf, info, 2 * sizeof(int), cudaMemcpyDeviceToHost, st()));
         THC_CUDA(cudaStreamSynchronize(st()));
         rank = inf[0];

@@ -1,4 +1,5 @@
-// gemm.cuh -- batched, shared-memory tiled SIMT GEMM with functor operands.
+// gemm.cuh -- batched, shared-memory tiled SIMT GEMM with functor operands
+// (real or complex accumulators).
 //
 // C[b](m, n) = sum_k A[b](m, k) * B[b](k, n), with A and B produced element by
 // element by loader functors (so the bond-2 MPO expansion, transposes and dtype
@@ -8,6 +9,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "scalar.cuh"
 
 namespace thc {
 
@@ -27,20 +29,20 @@ k_gemm(int M, int N, int K, LA la, LB lb, SC sc) {
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < TN; ++j) acc[i][j] = Acc(0);
+        for (int j = 0; j < TN; ++j) acc[i][j] = tzero<Acc>();
 
     for (int k0 = 0; k0 < K; k0 += BK) {
         // A tile: consecutive threads walk k (row-major A is contiguous in k)
         for (int i = tid; i < BM * BK; i += NT) {
             const int mm = i / BK, kk = i % BK;
             const int m = m0 + mm, k = k0 + kk;
-            As[kk][mm] = (m < M && k < K) ? Acc(la(b, m, k)) : Acc(0);
+            As[kk][mm] = (m < M && k < K) ? cvt<Acc>(la(b, m, k)) : tzero<Acc>();
         }
         // B tile: consecutive threads walk n (row-major B is contiguous in n)
         for (int i = tid; i < BK * BN; i += NT) {
             const int kk = i / BN, nn = i % BN;
             const int k = k0 + kk, n = n0 + nn;
-            Bs[kk][nn] = (k < K && n < N) ? Acc(lb(b, k, n)) : Acc(0);
+            Bs[kk][nn] = (k < K && n < N) ? cvt<Acc>(lb(b, k, n)) : tzero<Acc>();
         }
         __syncthreads();
 #pragma unroll
@@ -140,7 +142,7 @@ inline cudaError_t launch_gemm(int batch, int M, int N, int K, const LA& la, con
         }
     }
     constexpr int BM = 64, BN = 64, TM = 4, TN = 4;
-    constexpr int BK = sizeof(Acc) == 8 ? 8 : 16;
+    constexpr int BK = sizeof(Acc) >= 8 ? 8 : 16;
     dim3 grid(ceil_div(N, BN), ceil_div(M, BM), batch);
     k_gemm<Acc, BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, st>>>(M, N, K, la, lb, sc);
     return cudaGetLastError();

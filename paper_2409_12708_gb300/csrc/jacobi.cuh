@@ -1,11 +1,11 @@
 // jacobi.cuh -- truncated SVD of one compression step (Fig. 3, SVD sweep).
 //
-// Input per term: Z (p x n, row-major) with Z^T Z = C^T C, where C is the site
+// Input per term: Z (p x n, row-major) with Z^H Z = C^H C, where C is the site
 // matrix [(chi_l, n_phys) x k] being truncated (Z = R from a Householder QR of
 // C when C is tall, Z = C otherwise).  One-sided Jacobi (Hestenes) rotates
 // pairs of rows of Z until all rows are mutually orthogonal; rotations are
-// orthogonal, so Z^T Z = C^T C is preserved and the rows end up as
-// sigma_j v_j^T with v_j the right singular vectors of C.  Rows are visited in
+// unitary, so Z^H Z = C^H C is preserved and the rows end up as
+// sigma_j v_j^H with v_j the right singular vectors of C (v_j^T for real C).  Rows are visited in
 // a block ordering: blocks of R rows play a round-robin tournament, and one
 // warp holds the 2R rows of a block pair in registers while it rotates their
 // pairs, so shared-memory traffic is one read and write per R rotations of a
@@ -16,17 +16,19 @@
 // the truncation rule (cap D_max; with tol > 0 the smallest k whose discarded
 // weight is at most tol^2 of the total).
 //
-// Finalisation: with V_k the kept normalised rows, U = C V_k is normalised
-// column by column and the carried matrix becomes M = N (I - F) V_k^T with
-// F = V_k^T V_k - I (N = column norms of C V_k).  Then U M = C V_k (I-F) V_k^T,
-// the orthogonal projector onto span(V_k) to second order in F, so the state
-// is reproduced to rounding error even though the Jacobi rows are orthogonal
-// only to the convergence threshold.
+// Finalisation: with W the kept normalised rows (w_j = v_j^H), U = C W^H is
+// normalised column by column and the carried matrix becomes
+// M = N (I - F) W with F = W W^H - I (N = column norms of C W^H).  Then
+// U M = C W^H (I - F) W, the orthogonal projector onto span(V_k) to second
+// order in F, so the state is reproduced to rounding error even though the
+// Jacobi rows are orthogonal only to the convergence threshold.  (Real rows:
+// conjugation is the identity.)
 #pragma once
 
 #include <type_traits>
 
 #include "common.cuh"
+#include "scalar.cuh"
 
 namespace thc {
 
@@ -132,7 +134,7 @@ __device__ __forceinline__ void load_row(T (&x)[NPL], const T* row, bool ok, int
                     for (int e = 0; e < VEC; ++e) x[q * VEC + e] = pu[e];
                 } else {
 #pragma unroll
-                    for (int e = 0; e < VEC; ++e) x[q * VEC + e] = T(0);
+                    for (int e = 0; e < VEC; ++e) x[q * VEC + e] = tzero<T>();
                 }
             }
             return;
@@ -141,7 +143,7 @@ __device__ __forceinline__ void load_row(T (&x)[NPL], const T* row, bool ok, int
 #pragma unroll
     for (int i = 0; i < NPL; ++i) {
         const int c = lane + 32 * i;
-        x[i] = (ok && c < n) ? row[c] : T(0);
+        x[i] = (ok && c < n) ? row[c] : tzero<T>();
     }
 }
 
@@ -186,21 +188,27 @@ __device__ __forceinline__ double fast_rsqrt(double x) { return rsqrt(x); }
 // norms above the floor is rotated so that the two rows become orthogonal.
 //   * nrm holds the squared norms of the 2R rows (the same in every lane): they
 //     are computed exactly when a visit loads its rows and then updated with
-//     the rotation identities |a'|^2 = |a|^2 - t (a.b), |b'|^2 = |b|^2 + t (a.b).
-//   * The K dot products a.b are reduced by a reduce-scatter butterfly: each
-//     level hands half of the remaining values to the partner lane, so pair
-//     k's dot ends on the 32/K lanes with k = lane / (32/K).
+//     the rotation identities |a'|^2 = |a|^2 - t |a.b|, |b'|^2 = |b|^2 + t |a.b|.
+//   * The K dot products a.b = sum a conj(b) are reduced by a reduce-scatter
+//     butterfly: each level hands half of the remaining values to the partner
+//     lane, so pair k's dot ends on the 32/K lanes with k = lane / (32/K).
 //   * Those lanes decide and parametrise pair k's rotation in the storage
-//     precision (float64 is scarce on this part); c, s and t (a.b) are
-//     broadcast from the first lane of each group.
+//     precision (float64 is scarce on this part); c, s, t |a.b| (and the phase
+//     of a.b for complex rows) are broadcast from the first lane of each group.
 // The rotation is the classical one-sided Jacobi rotation (Hestenes): with
 // alpha = |a|^2, beta = |b|^2, gamma = a.b, zeta = (beta - alpha) / (2 gamma),
-// t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1 + t^2), s = c t.
-// A pair is rotated when gamma^2 > rot_tol^2 alpha beta.  t may carry a few
-// units of rounding; c gets one Newton step, so that c^2 + s^2 = 1 holds to
-// rounding and the rotation stays orthogonal.
+// t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1 + t^2), s = c t:
+// a' = c a - s b, b' = s a + c b.  Complex rows first take b to e b with
+// e = gamma / |gamma|, which makes the dot real (|gamma|), so the same real
+// rotation applies: a' = c a - s e b, b' = s conj(e) a + c b.  A pair is
+// rotated when |gamma|^2 > rot_tol^2 alpha beta.  t may carry a few units of
+// rounding; c gets one Newton step, so that c^2 + s^2 = 1 holds to rounding
+// and the rotation stays unitary.
 template <class T, int NPL, int NR, class PM>
-__device__ __forceinline__ int rotate_regs(T (&X)[NR][NPL], T (&nrm)[NR], unsigned vrows, T rt2, T floor2) {
+__device__ __forceinline__ int rotate_regs(T (&X)[NR][NPL], real_t<T> (&nrm)[NR], unsigned vrows, real_t<T> rt2,
+                                           real_t<T> floor2) {
+    using RT = real_t<T>;
+    constexpr bool CX = is_complex_v<T>;
     constexpr int K = PM::K;
     static_assert(K == 1 || K == 2 || K == 4 || K == 8, "pairs per step");
     const int lane = threadIdx.x & 31;
@@ -209,9 +217,9 @@ __device__ __forceinline__ int rotate_regs(T (&X)[NR][NPL], T (&nrm)[NR], unsign
     static_for<0, K>([&](auto kc) {
         constexpr int k = decltype(kc)::value;
         constexpr int a = PM::a(k), b = PM::b(k);
-        T g = T(0);
+        T g = tzero<T>();
 #pragma unroll
-        for (int i = 0; i < NPL; ++i) g += X[a][i] * X[b][i];
+        for (int i = 0; i < NPL; ++i) g += tconj_mul(X[b][i], X[a][i]);
         v[k] = g;
         pvalid |= ((vrows >> a) & (vrows >> b) & 1u) << k;
     });
@@ -227,15 +235,15 @@ __device__ __forceinline__ int rotate_regs(T (&X)[NR][NPL], T (&nrm)[NR], unsign
             if (i < half) {
                 const T send = upper ? v[i] : v[half + i];
                 const T keep = upper ? v[half + i] : v[i];
-                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                v[i] = keep + shfl_xor(send, o);
             }
         }
     }
     T ga = v[0];
 #pragma unroll
-    for (int o = 32 / K / 2; o >= 1; o >>= 1) ga += __shfl_xor_sync(0xffffffffu, ga, o);
+    for (int o = 32 / K / 2; o >= 1; o >>= 1) ga += shfl_xor(ga, o);
     const int my_pair = lane / (32 / K);
-    T al = T(0), be = T(0);
+    RT al = RT(0), be = RT(0);
     static_for<0, K>([&](auto kc) {
         constexpr int k = decltype(kc)::value;
         if (k == my_pair) {
@@ -243,20 +251,30 @@ __device__ __forceinline__ int rotate_regs(T (&X)[NR][NPL], T (&nrm)[NR], unsign
             be = nrm[PM::b(k)];
         }
     });
-    T c = T(1), s = T(0), tg = T(0);
+    RT c = RT(1), s = RT(0), tg = RT(0);
+    T ph = tone<T>();  // phase e of gamma (complex rows only)
     bool rot = false;
-    if (((pvalid >> my_pair) & 1u) && al > floor2 && be > floor2 && ga * ga > rt2 * (al * be)) {
-        const T zeta = fast_div(be - al, T(2) * ga);
-        const T az = zeta < T(0) ? -zeta : zeta;
-        const T q = T(1) + zeta * zeta;
-        const T root = az < T(1e18) ? q * fast_rsqrt(q) : az;
-        const T t = fast_div(tcopysign(T(1), zeta), az + root);
-        const T u = T(1) + t * t;
-        T cc = fast_rsqrt(u);
-        cc = cc * (T(1.5) - T(0.5) * u * cc * cc);
+    const RT g2 = tabs2(ga);
+    if (((pvalid >> my_pair) & 1u) && al > floor2 && be > floor2 && g2 > rt2 * (al * be)) {
+        RT gr;  // the dot after the phase: gamma (real rows) or |gamma| (complex rows)
+        if constexpr (CX) {
+            const RT inv = fast_rsqrt(g2);
+            gr = g2 * inv;
+            ph = tscale(ga, inv);
+        } else {
+            gr = ga;
+        }
+        const RT zeta = fast_div(be - al, RT(2) * gr);
+        const RT az = zeta < RT(0) ? -zeta : zeta;
+        const RT q = RT(1) + zeta * zeta;
+        const RT root = az < RT(1e18) ? q * fast_rsqrt(q) : az;
+        const RT t = fast_div(tcopysign(RT(1), zeta), az + root);
+        const RT u = RT(1) + t * t;
+        RT cc = fast_rsqrt(u);
+        cc = cc * (RT(1.5) - RT(0.5) * u * cc * cc);
         c = cc;
         s = cc * t;
-        tg = t * ga;
+        tg = t * gr;
         rot = true;
     }
     const unsigned bal = __ballot_sync(0xffffffffu, rot);
@@ -266,14 +284,24 @@ __device__ __forceinline__ int rotate_regs(T (&X)[NR][NPL], T (&nrm)[NR], unsign
         constexpr int a = PM::a(k), b = PM::b(k);
         constexpr int src = k * (32 / K);
         if ((bal >> src) & 1u) {
-            const T ck = __shfl_sync(0xffffffffu, c, src);
-            const T sk = __shfl_sync(0xffffffffu, s, src);
-            const T tgk = __shfl_sync(0xffffffffu, tg, src);
+            const RT ck = __shfl_sync(0xffffffffu, c, src);
+            const RT sk = __shfl_sync(0xffffffffu, s, src);
+            const RT tgk = __shfl_sync(0xffffffffu, tg, src);
+            if constexpr (CX) {
+                const T e = shfl(ph, src);
 #pragma unroll
-            for (int i = 0; i < NPL; ++i) {
-                const T x = X[a][i], y = X[b][i];
-                X[a][i] = ck * x - sk * y;
-                X[b][i] = sk * x + ck * y;
+                for (int i = 0; i < NPL; ++i) {
+                    const T x = X[a][i], y = X[b][i];
+                    X[a][i] = tscale(x, ck) - tscale(e * y, sk);
+                    X[b][i] = tscale(tconj_mul(e, x), sk) + tscale(y, ck);
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < NPL; ++i) {
+                    const T x = X[a][i], y = X[b][i];
+                    X[a][i] = ck * x - sk * y;
+                    X[b][i] = sk * x + ck * y;
+                }
             }
             nrm[a] -= tgk;
             nrm[b] += tgk;
@@ -314,7 +342,8 @@ __device__ __forceinline__ void cta_copy(T* dst, const T* src, long count) {
 // rotation.  Rows with ||z||^2 <= floor2 are numerically zero (below the
 // rounding level of the matrix they came from) and are not rotated.
 template <class T, int NPL, int R>
-__device__ int jacobi_sweep_reg(const Rows<T>& rows, int p, int n, bool vec, T rt2, T floor2) {
+__device__ int jacobi_sweep_reg(const Rows<T>& rows, int p, int n, bool vec, real_t<T> rt2, real_t<T> floor2) {
+    using RT = real_t<T>;
     static_assert(R >= 1 && R <= 4, "rows per block");
     const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int nbk = ceil_div(p, R);
@@ -325,7 +354,7 @@ __device__ int jacobi_sweep_reg(const Rows<T>& rows, int p, int n, bool vec, T r
         for (int bp = wid; bp < P2 / 2; bp += nw) {
             const int A = rr_player(bp, rr, P2), Bk = rr_player(P2 - 1 - bp, rr, P2);
             T X[2 * R][NPL];
-            T nrm[2 * R];
+            RT nrm[2 * R];
             unsigned vrows = 0;
 #pragma unroll
             for (int i = 0; i < 2 * R; ++i) {
@@ -334,9 +363,9 @@ __device__ int jacobi_sweep_reg(const Rows<T>& rows, int p, int n, bool vec, T r
                 const bool ok = blk < nbk && row < p;
                 vrows |= (ok ? 1u : 0u) << i;
                 load_row<T, NPL>(X[i], ok ? rows(row) : rows.Zs, ok, n, vec);
-                T s2 = T(0);
+                RT s2 = RT(0);
 #pragma unroll
-                for (int e = 0; e < NPL; ++e) s2 += X[i][e] * X[i][e];
+                for (int e = 0; e < NPL; ++e) s2 += tabs2(X[i][e]);
                 nrm[i] = s2;
             }
 #pragma unroll
@@ -377,7 +406,8 @@ __device__ int jacobi_rows(const Rows<T>& rows, int p, int n, bool vec, double r
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         if (threadIdx.x == 0) *nrot_sh = 0;
         __syncthreads();
-        const int myrot = jacobi_sweep_reg<T, NPL, R>(rows, p, n, vec, T(rot_tol * rot_tol), T(floor2));
+        const int myrot = jacobi_sweep_reg<T, NPL, R>(rows, p, n, vec, real_t<T>(rot_tol * rot_tol),
+                                                      real_t<T>(floor2));
         if (lane == 0 && myrot) atomicAdd(nrot_sh, myrot);
         __syncthreads();
         const int total = *nrot_sh;
@@ -422,10 +452,11 @@ __global__ void __launch_bounds__(JacobiCfg<T, NPL>::threads) k_jacobi_select(Ja
     // The Frobenius norm (invariant under the rotations) of the scaled matrix
     // then sets the rounding floor.
     __shared__ double red[32];
-    T tmax = T(0);
+    using RT = real_t<T>;
+    RT tmax = RT(0);
     for (int r = wid; r < p; r += nw) {
         const T* z = rows(r);
-        for (int c = lane; c < n; c += 32) tmax = fmax(tmax, z[c] < T(0) ? -z[c] : z[c]);
+        for (int c = lane; c < n; c += 32) tmax = fmax(tmax, tmaxabs(z[c]));
     }
     const double amax = block_max((double)tmax, red);
     double scale = 1.0;
@@ -434,20 +465,20 @@ __global__ void __launch_bounds__(JacobiCfg<T, NPL>::threads) k_jacobi_select(Ja
         frexp(amax, &ex);
         scale = ldexp(1.0, -ex);
     }
-    T tpart = T(0);
+    RT tpart = RT(0);
     {
-        const T sc = T(scale);
+        const RT sc = RT(scale);
         for (int r = wid; r < p; r += nw) {
             T* z = rows(r);
             for (int c = lane; c < n; c += 32) {
-                const T v = z[c] * sc;
+                const T v = tscale(z[c], sc);
                 z[c] = v;
-                tpart += v * v;
+                tpart += tabs2(v);
             }
         }
     }
     const double fro2 = block_sum((double)tpart, red);
-    const double floor2 = Real<T>::eps * Real<T>::eps * fro2;
+    const double floor2 = Real<RT>::eps * Real<RT>::eps * fro2;
     const int sweeps = jacobi_rows<T, NPL>(rows, p, n, vec, job.rot_tol, floor2, job.max_sweeps, &nrot_sh,
                                            job.status, job.dbg);
     if (tid == 0 && job.dbg) {  // sweep statistics: all matrices, and those with p >= 128
@@ -464,8 +495,8 @@ __global__ void __launch_bounds__(JacobiCfg<T, NPL>::threads) k_jacobi_select(Ja
     // float64
     for (int r = wid; r < p; r += nw) {
         const T* z = rows(r);
-        T acc = T(0);
-        for (int c = lane; c < n; c += 32) acc += z[c] * z[c];
+        RT acc = RT(0);
+        for (int c = lane; c < n; c += 32) acc += tabs2(z[c]);
         const double a = warp_sum((double)acc);
         if (lane == 0) s2[r] = a;
     }
@@ -509,7 +540,7 @@ __global__ void __launch_bounds__(JacobiCfg<T, NPL>::threads) k_jacobi_select(Ja
     const int k = kkeep_sh;
     // rows at or below twice the rounding floor are dropped (never rotated rows are
     // below the floor, so a kept row is always orthogonal to the threshold)
-    const double thresh = 2.0 * Real<T>::eps * sqrt(fro2);
+    const double thresh = 2.0 * Real<RT>::eps * sqrt(fro2);
     T* V = job.V + (long)b * job.strideV;
     double* sv = job.sv + (long)b * job.strideSv;
     for (int j = wid; j < kout; j += nw) {
@@ -521,10 +552,10 @@ __global__ void __launch_bounds__(JacobiCfg<T, NPL>::threads) k_jacobi_select(Ja
             if (!(sig > thresh)) row = -1;
         }
         if (lane == 0) sv[j] = row >= 0 ? sig / scale : 0.0;
-        const T inv = row >= 0 ? T(1.0 / sig) : T(0);
+        const RT inv = row >= 0 ? RT(1.0 / sig) : RT(0);
         const T* z = row >= 0 ? rows(row) : nullptr;
         const int* cm = job.colmap ? job.colmap + (long)b * n : nullptr;
-        for (int c = lane; c < n; c += 32) V[(long)j * n + (cm ? cm[c] : c)] = z ? z[c] * inv : T(0);
+        for (int c = lane; c < n; c += 32) V[(long)j * n + (cm ? cm[c] : c)] = z ? tscale(z[c], inv) : tzero<T>();
     }
 }
 
@@ -540,14 +571,11 @@ __global__ void __launch_bounds__(256) k_unit_columns(T* U, long strideU, int mU
     if (j >= kout) return;
     U += (long)b * strideU;
     double acc = 0.0;
-    for (int r = 0; r < mU; ++r) {
-        const double x = U[(long)r * kout + j];
-        acc += x * x;
-    }
+    for (int r = 0; r < mU; ++r) acc += (double)tabs2(U[(long)r * kout + j]);
     const double nrm = sqrt(acc);
-    const T inv = nrm > 0.0 ? T(1.0 / nrm) : T(0);
-    for (int r = 0; r < mU; ++r) U[(long)r * kout + j] *= inv;
-    nu[(long)b * strideNu + j] = nrm > 0.0 ? T(nrm) : T(0);
+    const real_t<T> inv = nrm > 0.0 ? real_t<T>(1.0 / nrm) : real_t<T>(0);
+    for (int r = 0; r < mU; ++r) U[(long)r * kout + j] = tscale(U[(long)r * kout + j], inv);
+    nu[(long)b * strideNu + j] = nrm > 0.0 ? treal<T>(real_t<T>(nrm)) : tzero<T>();
 }
 
 // A-operand of M = diag(nu) (I - F') V: element (i, l) = nu_i (delta_il - F'_il),
@@ -562,9 +590,9 @@ struct CorrA {
     __device__ __forceinline__ T operator()(int b, int i, int l) const {
         const T f = F[(long)b * sF + (long)i * k + l];
         const T fii = F[(long)b * sF + (long)i * k + i];
-        if (fii == T(0)) return T(0);  // dropped row: M row stays zero
-        const T fp = (i == l) ? f - T(1) : f;
-        return nu[(long)b * sNu + i] * ((i == l ? T(1) : T(0)) - fp);
+        if (fii == tzero<T>()) return tzero<T>();  // dropped row: M row stays zero
+        const T fp = (i == l) ? f - tone<T>() : f;
+        return nu[(long)b * sNu + i] * ((i == l ? tone<T>() : tzero<T>()) - fp);
     }
 };
 

@@ -2,22 +2,26 @@
 //
 // A (m x n, column-major, leading dimension ld, in global memory) is factored
 // as A = Q R with Q = H_0 H_1 ... H_{kk-1}, kk = min(m, n),
-// H_j = I - tau_j v_j v_j^T, v_j(j) = 1, v_j(i < j) = 0 (Golub & Van Loan,
-// Householder QR; the blocked form uses the compact WY representation
-// H_0 ... H_{b-1} = I - V T V^T of Schreiber & Van Loan).  Panels of nb columns
-// are factored in shared memory; the trailing columns are updated in groups of
-// QR_QG columns straight from global memory with register-tiled products
-// (W = V^T Y, W <- T^T W, Y -= V W), so each group is read twice and written
-// once per panel.
+// H_j = I - tau_j v_j v_j^H, v_j(j) = 1, v_j(i < j) = 0 (Golub & Van Loan,
+// Householder QR; for complex A the reflector of LAPACK's convention, with a
+// real beta and a complex tau, and H_j^H applied to the trailing columns; the
+// blocked form uses the compact WY representation H_0 ... H_{b-1} =
+// I - V T V^H of Schreiber & Van Loan).  Panels of nb columns are factored in
+// shared memory; the trailing columns are updated in groups of QR_QG columns
+// straight from global memory with register-tiled products
+// (W = V^H Y, W <- T^H W, Y -= V W), so each group is read twice and written
+// once per panel.  Real and complex scalars share the code (scalar.cuh).
 //
 // Modes (after the factorisation):
 //   QR_L_AND_Q : writes L = R^T (n x kk, row-major) and overwrites the first kk
 //                columns of A with the thin Q (used to right-canonicalise a site:
-//                A holds X^T, so X = L Q^T and Q^T becomes the site tensor).
+//                A holds X^T, so X = L Q^T and Q^T becomes the site tensor; for
+//                complex X the plain transpose keeps Q^T's rows orthonormal).
 //   QR_R_ROWS  : writes R (n x n, row-major, zero below the diagonal); m >= n.
 #pragma once
 
 #include "common.cuh"
+#include "scalar.cuh"
 
 namespace thc {
 
@@ -51,7 +55,8 @@ constexpr int QR_QG = 16;        // trailing columns per group
 // the columns a warp reads at once fall in distinct bank groups.
 template <class T>
 __host__ __device__ inline int qr_ldp(int m) {
-    return sizeof(T) == 4 ? (m + 31) / 32 * 32 + 4 : (m + 15) / 16 * 16 + 2;
+    constexpr int e16 = 16 / (int)sizeof(T), e128 = 128 / (int)sizeof(T);
+    return (m + e128 - 1) / e128 * e128 + e16;
 }
 
 // Reflector rows per lane in the register-tiled products (lane (ig, cg) owns
@@ -63,15 +68,24 @@ __host__ inline size_t qr_smem_bytes(int m, int nb, int n) {
     const size_t cap = 8 * qr_ni(nb);  // rows of W per warp partial
     const size_t base = 64 * sizeof(double) + (size_t)nb * qr_ldp<T>(m) * sizeof(T) + 2 * (size_t)nb * nb * sizeof(T) +
                         ((size_t)(QR_THREADS / 32) * cap * QR_QG + 2 * cap * QR_QG) * sizeof(T);
-    // pivoting state: nb float64 norms, nb + n metrics / norms, two n-int column maps
-    const size_t piv = (size_t)nb * sizeof(double) + (size_t)(nb + n) * sizeof(T) + 2 * (size_t)n * sizeof(int);
+    // pivoting state: nb float64 norms, nb + n (real) metrics / norms, two n-int column maps
+    const size_t piv = (size_t)nb * sizeof(double) + (size_t)(nb + n) * sizeof(real_t<T>) +
+                       2 * (size_t)n * sizeof(int);
     return base + ((piv + 15) & ~(size_t)15);
 }
 
 // four consecutive elements with 16-byte accesses (p 16-byte aligned)
 template <class T>
 __device__ __forceinline__ void ld4(T (&x)[4], const T* p) {
-    if constexpr (sizeof(T) == 4) {
+    if constexpr (is_complex_v<T>) {
+        constexpr int NV = 4 * (int)sizeof(T) / 16;  // 16-byte words
+        uint4 u[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) u[q] = reinterpret_cast<const uint4*>(p)[q];
+        const T* pu = reinterpret_cast<const T*>(u);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) x[q] = pu[q];
+    } else if constexpr (sizeof(T) == 4) {
         const float4 u = *reinterpret_cast<const float4*>(p);
         x[0] = u.x;
         x[1] = u.y;
@@ -88,7 +102,15 @@ __device__ __forceinline__ void ld4(T (&x)[4], const T* p) {
 }
 template <class T>
 __device__ __forceinline__ void st4(T* p, const T (&x)[4]) {
-    if constexpr (sizeof(T) == 4) {
+    if constexpr (is_complex_v<T>) {
+        constexpr int NV = 4 * (int)sizeof(T) / 16;
+        uint4 u[NV];
+        T* pu = reinterpret_cast<T*>(u);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) pu[q] = x[q];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) reinterpret_cast<uint4*>(p)[q] = u[q];
+    } else if constexpr (sizeof(T) == 4) {
         *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
     } else {
         *reinterpret_cast<double2*>(p) = make_double2(x[0], x[1]);
@@ -102,7 +124,7 @@ __device__ __forceinline__ void ld4_col(T (&x)[4], const T* col, int r, int R, b
         ld4(x, col + r);
     } else {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) x[q] = r + q < R ? col[r + q] : T(0);
+        for (int q = 0; q < 4; ++q) x[q] = r + q < R ? col[r + q] : tzero<T>();
     }
 }
 template <class T>
@@ -153,6 +175,24 @@ struct SqAcc<float> {
     }
 };
 
+// complex: both parts of every entry go through the accumulator of the real type
+template <class R>
+struct SqAcc<cplx<R>> {
+    SqAcc<R> a;
+    __device__ __forceinline__ void add(cplx<R> x) {
+        a.add(x.x);
+        a.add(x.y);
+    }
+    __device__ __forceinline__ double warp_total() { return a.warp_total(); }
+};
+
+// |x|^2 evaluated in float64
+template <class T>
+__device__ __forceinline__ double dabs2(T x) {
+    if constexpr (is_complex_v<T>) return (double)x.x * (double)x.x + (double)x.y * (double)x.y;
+    else return (double)x * (double)x;
+}
+
 // Squared norm of y[r0 .. R) by one warp (every lane gets the total).  In
 // float32, squares of entries below ~1e-19 underflow or lose their precision
 // (residues of rank-deficient columns are of that size), which would make the
@@ -164,9 +204,9 @@ __device__ __forceinline__ double col_norm2(const T* y, int r0, int R) {
     SqAcc<T> a;
     for (int r = r0 + lane; r < R; r += 32) a.add(y[r]);
     double t = a.warp_total();
-    if (sizeof(T) == 4 && t < 1e-30) {
+    if (sizeof(real_t<T>) == 4 && t < 1e-30) {
         double s = 0.0;
-        for (int r = r0 + lane; r < R; r += 32) s += (double)y[r] * (double)y[r];
+        for (int r = r0 + lane; r < R; r += 32) s += dabs2(y[r]);
         t = warp_sum(s);
     }
     return t;
@@ -176,7 +216,7 @@ __device__ __forceinline__ double col_norm2(const T* y, int r0, int R) {
 // explicitly in shared memory (column i at P + i*ldp: zeros above row i, 1 at
 // row i, zero rows from R up to the next multiple of 4).
 //
-// (1) Per-warp partial products Wp[w] = V^T Y over the rows of warp w for the
+// (1) Per-warp partial products Wp[w] = V^H Y over the rows of warp w for the
 //     QR_QG columns whose bases col(c) returns (c < QR_QG; null: no column).
 //     Lane (ig, cg) owns rows ig + 8 ii of W and columns 4 cg .. 4 cg + 3; each
 //     step takes four rows of V and Y with 16-byte loads.
@@ -191,7 +231,7 @@ __device__ __forceinline__ void qr_vty(const T* P, int ldp, int pw, int R, T* Wp
 #pragma unroll
     for (int ii = 0; ii < NI; ++ii)
 #pragma unroll
-        for (int jj = 0; jj < 4; ++jj) acc[ii][jj] = T(0);
+        for (int jj = 0; jj < 4; ++jj) acc[ii][jj] = tzero<T>();
     const T* yc[4];
 #pragma unroll
     for (int jj = 0; jj < 4; ++jj) yc[jj] = col(4 * cg + jj);
@@ -203,7 +243,7 @@ __device__ __forceinline__ void qr_vty(const T* P, int ldp, int pw, int R, T* Wp
                 ld4(v[ii], P + (ig + 8 * ii) * ldp + r);
             } else {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) v[ii][q] = T(0);
+                for (int q = 0; q < 4; ++q) v[ii][q] = tzero<T>();
             }
         }
 #pragma unroll
@@ -212,7 +252,7 @@ __device__ __forceinline__ void qr_vty(const T* P, int ldp, int pw, int R, T* Wp
                 ld4_col(y[jj], yc[jj], r, R, vec);
             } else {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) y[jj][q] = T(0);
+                for (int q = 0; q < 4; ++q) y[jj][q] = tzero<T>();
             }
         }
 #pragma unroll
@@ -220,7 +260,7 @@ __device__ __forceinline__ void qr_vty(const T* P, int ldp, int pw, int R, T* Wp
 #pragma unroll
             for (int ii = 0; ii < NI; ++ii)
 #pragma unroll
-                for (int jj = 0; jj < 4; ++jj) acc[ii][jj] += v[ii][q] * y[jj][q];
+                for (int jj = 0; jj < 4; ++jj) acc[ii][jj] += tconj_mul(v[ii][q], y[jj][q]);
     }
 #pragma unroll
     for (int ii = 0; ii < NI; ++ii)
@@ -233,20 +273,20 @@ template <class T>
 __device__ __forceinline__ void qr_sum_partials(const T* Wp, T* W0, int pw, int cap) {
     const int nw = blockDim.x >> 5;
     for (int o = threadIdx.x; o < pw * QR_QG; o += blockDim.x) {
-        T s = 0;
+        T s = tzero<T>();
         for (int w = 0; w < nw; ++w) s += Wp[w * cap * QR_QG + o];
         W0[o] = s;
     }
 }
 
-// (3) W1 = T^T W0 (factorisation) or T W0 (forming Q); T upper triangular
+// (3) W1 = T^H W0 (factorisation) or T W0 (forming Q); T upper triangular
 template <class T>
 __device__ __forceinline__ void qr_t_times(const T* Tm, int nbT, const T* W0, T* W1, int pw, bool transpose) {
     for (int o = threadIdx.x; o < pw * QR_QG; o += blockDim.x) {
         const int i = o / QR_QG, c = o % QR_QG;
-        T s = 0;
+        T s = tzero<T>();
         if (transpose) {
-            for (int l = 0; l <= i; ++l) s += Tm[l * nbT + i] * W0[l * QR_QG + c];
+            for (int l = 0; l <= i; ++l) s += tconj_mul(Tm[l * nbT + i], W0[l * QR_QG + c]);
         } else {
             for (int l = i; l < pw; ++l) s += Tm[i * nbT + l] * W0[l * QR_QG + c];
         }
@@ -273,19 +313,19 @@ __device__ __forceinline__ void qr_sub_vw(const T* P, int ldp, int pw, int R, co
             yc[jj] = c < ncols ? col(c) : nullptr;
             if (IDENT) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) y[jj][q] = (r + q == cb + c) ? T(1) : T(0);
+                for (int q = 0; q < 4; ++q) y[jj][q] = (r + q == cb + c) ? tone<T>() : tzero<T>();
             } else if (yc[jj]) {
                 ld4_col(y[jj], yc[jj], r, R, vec);
             } else {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) y[jj][q] = T(0);
+                for (int q = 0; q < 4; ++q) y[jj][q] = tzero<T>();
             }
         }
         T acc[4][4];
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[jj][q] = T(0);
+            for (int q = 0; q < 4; ++q) acc[jj][q] = tzero<T>();
 #pragma unroll 4
         for (int i = 0; i < pw; ++i) {
             T vq[4], w[4];
@@ -305,9 +345,9 @@ __device__ __forceinline__ void qr_sub_vw(const T* P, int ldp, int pw, int R, co
     }
 }
 
-// Apply (H_p0 ... H_{p0+pw-1})^T (transpose=true, factorisation) or
+// Apply (H_p0 ... H_{p0+pw-1})^H (transpose=true, factorisation) or
 // H_p0 ... H_{p0+pw-1} (transpose=false, forming Q) to columns [c_begin, c_end)
-// of A, rows [p0, m), in groups of QR_QG columns: W = V^T Y, W <- T^T W (or
+// of A, rows [p0, m), in groups of QR_QG columns: W = V^H Y, W <- T^H W (or
 // T W), Y -= V W.  Every product step is 16-byte loads and an outer product
 // of 4-vectors.
 template <class T, int NI>
@@ -333,8 +373,8 @@ __device__ void qr_block_apply(T* A, int ld, int m, int p0, int pw, int c_begin,
 
 // Columns p0 .. p0+pw-1 of Q = H_0 ... H_{kk-1} [I; 0] once the later panels
 // are applied: rows p0.. of those columns are H_p0 ... H_{p0+pw-1} E with E the
-// identity columns, i.e. E - V (T V1^T) with V1 the top pw x pw block of V
-// (V^T E = V1^T); rows above p0 are zero.
+// identity columns, i.e. E - V (T V1^H) with V1 the top pw x pw block of V
+// (V^H E = V1^H); rows above p0 are zero.
 template <class T>
 __device__ void qr_form_panel(T* A, int ld, int m, int p0, int pw, const T* P, int ldp, const T* Tm, int nbT,
                               T* W0, T* W1, const int* cm, bool vec) {
@@ -343,7 +383,7 @@ __device__ void qr_form_panel(T* A, int ld, int m, int p0, int pw, const T* P, i
         const int gc = min(QR_QG, pw - cb);
         for (int o = threadIdx.x; o < pw * QR_QG; o += blockDim.x) {
             const int i = o / QR_QG, c = o % QR_QG;
-            W0[o] = c < gc ? P[i * ldp + cb + c] : T(0);
+            W0[o] = c < gc ? tconj(P[i * ldp + cb + c]) : tzero<T>();
         }
         __syncthreads();
         qr_t_times(Tm, nbT, W0, W1, pw, false);
@@ -354,7 +394,7 @@ __device__ void qr_form_panel(T* A, int ld, int m, int p0, int pw, const T* P, i
     }
     for (int i = threadIdx.x; i < pw * p0; i += blockDim.x) {
         const int c = i / p0, r = i % p0;
-        A[(long)QCOL(p0 + c) * ld + r] = T(0);
+        A[(long)QCOL(p0 + c) * ld + r] = tzero<T>();
     }
     __syncthreads();
 }
@@ -364,7 +404,7 @@ template <class T>
 __device__ __forceinline__ void qr_explicit_v(T* P, int ldp, int pw) {
     for (int o = threadIdx.x; o < pw * pw; o += blockDim.x) {
         const int i = o / pw, r = o % pw;  // column i, row r
-        if (r <= i) P[i * ldp + r] = (r == i) ? T(1) : T(0);
+        if (r <= i) P[i * ldp + r] = (r == i) ? tone<T>() : tzero<T>();
     }
 }
 
@@ -381,7 +421,8 @@ __device__ __forceinline__ void qr_explicit_v(T* P, int ldp, int pw) {
 // barrier), and every warp keeps the norms of all its columns current.
 template <class T>
 __device__ void qr_panel(T* P, int ldp, int R, int pw, T* Tm, int nb, T* psc, double* red, int* pmp, double* nb2,
-                         T* met) {
+                         real_t<T>* met) {
+    using RT = real_t<T>;
     __shared__ int ksh;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
@@ -397,7 +438,7 @@ __device__ void qr_panel(T* P, int ldp, int R, int pw, T* Tm, int nb, T* psc, do
             const double t = col_norm2(P + c * ldp, 1, R);
             if (lane == 0) {
                 nb2[c] = t;
-                met[c] = T((double)P[c * ldp] * (double)P[c * ldp] + t);
+                met[c] = RT(dabs2(P[c * ldp]) + t);
             }
         }
     }
@@ -407,7 +448,7 @@ __device__ void qr_panel(T* P, int ldp, int R, int pw, T* Tm, int nb, T* psc, do
         if (tid == 0) {
             int k = j;
             if (piv) {
-                T best = met[j];
+                RT best = met[j];
                 for (int c = j + 1; c < pw; ++c)
                     if (met[c] > best) {
                         best = met[c];
@@ -426,11 +467,20 @@ __device__ void qr_panel(T* P, int ldp, int R, int pw, T* Tm, int nb, T* psc, do
             T* xk = P + k * ldp;  // the column that becomes column j
             const double xn2 = piv ? nb2[j] : red[j & 1];
             const T alpha = xk[j];
-            T tau = T(0), scale = T(0);
-            const double a2 = (double)alpha * (double)alpha + xn2;
+            T tau = tzero<T>(), scale = tzero<T>();
+            const double a2 = dabs2(alpha) + xn2;
             // a sub-column below (1e-30)^2 (float32) is treated as zero
-            if (xn2 > 0.0 && a2 > (sizeof(T) == 4 ? 1e-60 : 0.0)) {
-                if (sizeof(T) == 4 && a2 >= 1e-36) {
+            if (xn2 > 0.0 && a2 > (sizeof(RT) == 4 ? 1e-60 : 0.0)) {
+                if constexpr (is_complex_v<T>) {
+                    // beta = -sign(Re alpha) |(alpha, x)| (real), tau = (beta - alpha) / beta,
+                    // scale = 1 / (alpha - beta), evaluated in float64
+                    const double ar = alpha.x, ai = alpha.y;
+                    const double beta = -copysign(sqrt(a2), ar);
+                    tau = T{RT((beta - ar) / beta), RT(-ai / beta)};
+                    const double zr = ar - beta, zi = ai, zz = zr * zr + zi * zi;
+                    scale = T{RT(zr / zz), RT(-zi / zz)};
+                    xk[j] = T{RT(beta), RT(0)};
+                } else if (sizeof(T) == 4 && a2 >= 1e-36) {
                     const T beta = -tcopysign(tsqrt(T(a2)), alpha);
                     tau = (beta - alpha) / beta;
                     scale = T(1) / (alpha - beta);
@@ -467,18 +517,19 @@ __device__ void qr_panel(T* P, int ldp, int R, int pw, T* Tm, int nb, T* psc, do
         if (piv) __syncthreads();
         for (int c = j + 1 + wid; c < pw; c += nw) {
             T* y = P + c * ldp;
-            if (tau != T(0)) {
+            if (tau != tzero<T>()) {
                 // x is scaled inside the dot: the product of two raw sub-columns
-                // would underflow in float32 for entries below ~1e-19
-                T s0 = T(0), s1 = T(0);
+                // would underflow in float32 for entries below ~1e-19.
+                // y <- H^H y = y - conj(tau) v (v^H y), v = (1, x scale)
+                T s0 = tzero<T>(), s1 = tzero<T>();
                 int r = j + 1 + lane;
                 for (; r + 32 < R; r += 64) {
-                    s0 += (x[r] * scale) * y[r];
-                    s1 += (x[r + 32] * scale) * y[r + 32];
+                    s0 += tconj_mul(x[r] * scale, y[r]);
+                    s1 += tconj_mul(x[r + 32] * scale, y[r + 32]);
                 }
-                if (r < R) s0 += (x[r] * scale) * y[r];
+                if (r < R) s0 += tconj_mul(x[r] * scale, y[r]);
                 const T sdot = warp_sum(s0 + s1) + y[j];
-                const T f = tau * sdot, fs = f * scale;
+                const T f = tconj(tau) * sdot, fs = f * scale;
                 for (int rr = j + 1 + lane; rr < R; rr += 32) y[rr] -= fs * x[rr];
                 __syncwarp();
                 if (lane == 0) y[j] -= f;
@@ -488,7 +539,7 @@ __device__ void qr_panel(T* P, int ldp, int R, int pw, T* Tm, int nb, T* psc, do
                 const double t = col_norm2(y, j + 2, R);
                 if (lane == 0) {
                     nb2[c] = t;
-                    met[c] = T((double)y[j + 1] * (double)y[j + 1] + t);
+                    met[c] = RT(dabs2(y[j + 1]) + t);
                 }
             } else if (c == j + 1) {
                 __syncwarp();
@@ -508,7 +559,7 @@ __device__ void qr_panel(T* P, int ldp, int R, int pw, T* Tm, int nb, T* psc, do
 }
 
 // T of the compact WY form of the panel (explicit V in P, tau_j on Tm's
-// diagonal): G = V^T V with the tiled product, then row i of T by one lane:
+// diagonal): G = V^H V with the tiled product, then row i of T by one lane:
 // T[i][j] = -tau_j sum_{l=i}^{j-1} T[i][l] G[l][j] for j > i (the columnwise
 // recursion of Schreiber & Van Loan, read by rows), zeros below the diagonal.
 template <class T, int NI>
@@ -521,7 +572,7 @@ __device__ void qr_t_matrix(const T* P, int ldp, int R, int pw, T* Tm, int nb, T
         for (int o = threadIdx.x; o < pw * QR_QG; o += blockDim.x) {
             const int i = o / QR_QG, c = o % QR_QG;
             if (cb + c < pw) {
-                T s = 0;
+                T s = tzero<T>();
                 for (int w = 0; w < nw; ++w) s += Wp[w * 8 * NI * QR_QG + o];
                 G[i * pw + cb + c] = s;
             }
@@ -530,11 +581,11 @@ __device__ void qr_t_matrix(const T* P, int ldp, int R, int pw, T* Tm, int nb, T
     }
     if (threadIdx.x < pw) {
         const int i = threadIdx.x;
-        for (int j = 0; j < i; ++j) Tm[i * nb + j] = T(0);
+        for (int j = 0; j < i; ++j) Tm[i * nb + j] = tzero<T>();
         for (int j = i + 1; j < pw; ++j) {
-            T s = 0;
+            T s = tzero<T>();
             for (int l = i; l < j; ++l) s += Tm[i * nb + l] * G[l * pw + j];
-            Tm[i * nb + j] = -Tm[j * nb + j] * s;
+            Tm[i * nb + j] = tzero<T>() - Tm[j * nb + j] * s;
         }
     }
     __syncthreads();
@@ -574,9 +625,10 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr(QRJob<T> job) {
     T* Wp = G + nb * nb;
     T* W0 = Wp + (size_t)nw * cap * QR_QG;
     T* W1 = W0 + (size_t)cap * QR_QG;
+    using RT = real_t<T>;
     double* nb2 = reinterpret_cast<double*>(W1 + (size_t)cap * QR_QG);
-    T* met = reinterpret_cast<T*>(nb2 + nb);
-    T* cnrm = met + nb;
+    RT* met = reinterpret_cast<RT*>(nb2 + nb);
+    RT* cnrm = met + nb;
     int* pm = reinterpret_cast<int*>(cnrm + n);
     int* pm2 = pm + n;
     // the column map in shared memory: the given one, or the order pivoting chooses
@@ -599,17 +651,17 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr(QRJob<T> job) {
             // largest ones
             for (int c = p0 + wid; c < n; c += nw) {
                 const T* col = A + (long)pm[c] * ld + p0;
-                T s2 = T(0);
-                for (int r = lane; r < R; r += 32) s2 += col[r] * col[r];
+                RT s2 = RT(0);
+                for (int r = lane; r < R; r += 32) s2 += tabs2(col[r]);
                 s2 = warp_sum(s2);
-                if (lane == 0) cnrm[c] = (s2 == s2) ? s2 : T(-1);
+                if (lane == 0) cnrm[c] = (s2 == s2) ? s2 : RT(-1);
             }
             __syncthreads();
             for (int c = p0 + tid; c < n; c += nt) {
-                const T v = cnrm[c];
+                const RT v = cnrm[c];
                 int rank = 0;
                 for (int q = p0; q < n; ++q) {
-                    const T w = cnrm[q];
+                    const RT w = cnrm[q];
                     rank += (w > v) || (w == v && q < c);
                 }
                 pm2[p0 + rank] = pm[c];
@@ -620,7 +672,7 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr(QRJob<T> job) {
         }
         for (int i = tid; i < pw * R4; i += nt) {
             const int c = i / R4, r = i % R4;
-            P[c * ldp + r] = r < R ? A[(long)QCOL(p0 + c) * ld + p0 + r] : T(0);
+            P[c * ldp + r] = r < R ? A[(long)QCOL(p0 + c) * ld + p0 + r] : tzero<T>();
         }
         __syncthreads();
         qr_panel(P, ldp, R, pw, Tm, nb, W0, red, piv ? pm + p0 : nullptr, nb2, met);
@@ -648,7 +700,7 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr(QRJob<T> job) {
     if (job.mode == QR_R_ROWS) {
         for (int i = tid; i < n * n; i += nt) {
             const int r = i / n, c = i % n;
-            out[i] = (r <= c && r < kk) ? A[(long)QCOL(c) * ld + r] : T(0);
+            out[i] = (r <= c && r < kk) ? A[(long)QCOL(c) * ld + r] : tzero<T>();
         }
         if (piv)
             for (int c = tid; c < n; c += nt) job.colmap[(long)b * n + c] = pm[c];
@@ -657,7 +709,7 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr(QRJob<T> job) {
     // QR_L_AND_Q: L = R^T (n x kk)
     for (int i = tid; i < n * kk; i += nt) {
         const int r = i / kk, c = i % kk;
-        out[i] = (c <= r) ? A[(long)QCOL(r) * ld + c] : T(0);
+        out[i] = (c <= r) ? A[(long)QCOL(r) * ld + c] : tzero<T>();
     }
     __syncthreads();
     // form Q in place, panels in reverse order
@@ -669,7 +721,7 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr(QRJob<T> job) {
         const int R4 = 4 * ceil_div(R, 4);
         for (int i = tid; i < pw * R4; i += nt) {
             const int c = i / R4, r = i % R4;
-            P[c * ldp + r] = r < R ? A[(long)QCOL(p0 + c) * ld + p0 + r] : T(0);
+            P[c * ldp + r] = r < R ? A[(long)QCOL(p0 + c) * ld + p0 + r] : tzero<T>();
         }
         for (int i = tid; i < nb * nb; i += nt) Tm[i] = Tw[pi * nb * nb + i];
         __syncthreads();
