@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--batch", type=int, default=0)
+    p.add_argument("--path", default="fp32", choices=["fp32", "tf32"],
+                   help="compute path of the headline (tf32: contractions on the tensor cores)")
     p.add_argument("--terms", type=int, default=0,
                    help="apply only the first TERMS terms per step (0 = all; for profiling slices)")
     p.add_argument("--no-profile", action="store_true", help="skip the CUDA-event profiled step")
@@ -348,9 +350,9 @@ def run_ours(args):
 
     def step():
         if args.terms > 0:
-            return B.thc_apply_H(*H, psi32, D_max=D, path="fp32", batch=args.batch, term_begin=0,
+            return B.thc_apply_H(*H, psi32, D_max=D, path=args.path, batch=args.batch, term_begin=0,
                                  term_end=args.terms)
-        return B.thc_apply_H(*H, psi32, D_max=D, path="fp32", batch=args.batch)
+        return B.thc_apply_H(*H, psi32, D_max=D, path=args.path, batch=args.batch)
 
     def barrier():
         if world > 1:
@@ -391,10 +393,10 @@ def run_ours(args):
             dH = [x.to("cuda", non_blocking=True) for x in hH]
             dp = [x.to("cuda", non_blocking=True) for x in hp]
             if args.terms > 0:
-                o = B.thc_apply_H(*dH, dp, D_max=D, path="fp32", batch=args.batch, term_begin=0,
+                o = B.thc_apply_H(*dH, dp, D_max=D, path=args.path, batch=args.batch, term_begin=0,
                                   term_end=args.terms)
             else:
-                o = B.thc_apply_H(*dH, dp, D_max=D, path="fp32", batch=args.batch)
+                o = B.thc_apply_H(*dH, dp, D_max=D, path=args.path, batch=args.batch)
             res = [x.to("cpu", non_blocking=True) for x in o]
             e1.record()
             e1.synchronize()
@@ -412,7 +414,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         prof = B.profile_read()
         B.profile_enable(False)
-    stats = {k: prof.pop(k) for k in list(prof) if k.startswith("jacobi_sweeps") or k.startswith("jacobi_budget")}
+    stats = {k: prof.pop(k) for k in list(prof)
+             if k.startswith("jacobi_sweeps") or k.startswith("jacobi_budget") or k == "tc_gemm_launches"}
 
     # ---- float32 vs plain float64 on the same leading slice of terms, every term
     # of the slice in flight at once on both paths (so both fill the GPU alike);
@@ -423,7 +426,7 @@ def run_ours(args):
         psi64 = [dev(a) for a in psi]
         n64 = min(args.slice_terms, T)
         res = {}
-        for pth, pp in (("fp32", psi32), ("fp64", psi64)):
+        for pth, pp in (("fp32", psi32), ("tf32", psi32), ("fp64", psi64)):
             B.thc_apply_H(*H, pp, D_max=D, path=pth, term_begin=0, term_end=min(n64, 8), batch=8)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -432,13 +435,19 @@ def run_ours(args):
             e1.record()
             e1.synchronize()
             res[pth] = (e0.elapsed_time(e1) / 1e3, o)
-        a = [x.double() for x in res["fp32"][1]]
         b = res["fp64"][1]
-        aa, bb, ab = B.mps_inner(a, a), B.mps_inner(b, b), B.mps_inner(a, b)
-        rel = float(np.sqrt(max(aa + bb - 2.0 * ab, 0.0) / bb))
-        s32, s64 = res["fp32"][0], res["fp64"][0]
+        bb = B.mps_inner(b, b)
+
+        def rel_to_fp64(pth):
+            a = [x.double() for x in res[pth][1]]
+            aa, ab = B.mps_inner(a, a), B.mps_inner(a, b)
+            return float(np.sqrt(max(aa + bb - 2.0 * ab, 0.0) / bb))
+
+        s32, s64, stf = res["fp32"][0], res["fp64"][0], res["tf32"][0]
         fp64 = {"terms": n64, "in_flight": n64, "fp64_terms_per_s": n64 / s64, "fp32_terms_per_s": n64 / s32,
-                "speedup_fp32_vs_fp64": s64 / s32, "fp32_rel_error_vs_fp64": rel,
+                "tf32_terms_per_s": n64 / stf, "speedup_fp32_vs_fp64": s64 / s32,
+                "speedup_tf32_vs_fp64": s64 / stf, "fp32_rel_error_vs_fp64": rel_to_fp64("fp32"),
+                "tf32_rel_error_vs_fp64": rel_to_fp64("tf32"),
                 "extrapolated_fp64_hpsi_s": s64 * T / n64,
                 "note": f"both paths on terms [0,{n64}) with all {n64} terms in flight; float64 H|psi> time "
                         f"extrapolated from the slice (labelled); relative distance of the float32 result "
@@ -485,7 +494,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "L": w["L"], "N": w["N"], "D_max": D, "terms": n_step,
-                   "path": "fp32", "l2": "flushed between steps (256 MiB write)",
+                   "path": args.path, "l2": "flushed between steps (256 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "hpsi_per_s": value / T,
         "gpu_launches": int(launches),
@@ -493,7 +502,7 @@ def run_ours(args):
         "roofline": roof,
         "clocks": clocks,
         "fp64": fp64,
-        "speedup_vs_fp64": fp64["speedup_fp32_vs_fp64"] if fp64 else None,
+        "speedup_vs_fp64": fp64["speedup_%s_vs_fp64" % args.path] if fp64 else None,
         "kernel_ms_per_step": {k: round(v["ms"], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])},
         "jacobi_sweeps_per_svd": {k: round(v["ms"] / max(v["launches"], 1), 2) for k, v in stats.items()
                                   if k.startswith("jacobi_sweeps")},

@@ -213,6 +213,28 @@ thc_status krylov_expm_apply(const thc_hamiltonian* H, const thc_mps* psi, doubl
                              const thc_opts* opts, thc_mps* out, double* lost_norm,
                              const thc_allocator* alloc, void* stream);
 
+/* The adjoint of the THC-MPO expectation value: E = <phi|H|psi> for H of Eq. 1
+ * with v of Eq. thc, contracted exactly (no compression) term by term through
+ * the bond-2 ladder MPOs of Sec. 3.1 (the 4N^2 Coulomb terms G_{mu s, nu s'} of
+ * Eq. G and the one-body terms (sum_p t_pq a+_{p s}) a_{q s}), with left and
+ * right environments; the derivatives are the reverse-mode contractions of
+ * the same networks (the paper computes no derivatives; this serves
+ * differentiation through H's factors and the state).
+ *  - phi, psi: real MPS (F64 on path FP64, F32 on FP32 / TF32), equal L, any
+ *    bonds up to 4096 (memory permitting).
+ *  - value: host double, E.
+ *  - grad_t [L*L], grad_chi [L*N], grad_zeta [N*N]: device float64, row-major
+ *    like t, chi, zeta; written with dE/dt_pq, dE/dchi^mu_p, dE/dzeta^{mu nu}
+ *    (every entry an independent variable); each may be NULL.
+ *  - grad_psi: optional output MPS (psi's bonds and dtype), site i =
+ *    dE/d(site i of psi); NULL to skip.
+ *  - opts: path and batch (terms in flight) are used; D_max and tol are not
+ *    (nothing is truncated).
+ * Errors: THC_EINVAL, THC_EUNSUPPORTED (complex MPS), THC_ENOMEM, THC_ECUDA. */
+thc_status thc_expect_grad(const thc_hamiltonian* H, const thc_mps* phi, const thc_mps* psi,
+                           const thc_opts* opts, double* value, double* grad_t, double* grad_chi,
+                           double* grad_zeta, thc_mps* grad_psi, const thc_allocator* alloc, void* stream);
+
 /* Eigen-decomposition t = U diag(lambda) U^T of the one-body integrals (App. D,
  * Eq. t_diagonalization) by a float64 Jacobi kernel: t device [L*L] row-major,
  * lambda device [L] ascending, u device [L*L] row-major with column i the

@@ -83,6 +83,8 @@ def _load():
                               P(thc_mps), P(C.c_double), P(thc_allocator), C.c_void_p],
         "thc_kinetic_factors": [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
         "mps_inner_noalloc": [P(thc_mps), P(thc_mps), P(C.c_double), C.c_void_p],
+        "thc_expect_grad": [P(thc_hamiltonian), P(thc_mps), P(thc_mps), P(thc_opts), P(C.c_double), C.c_void_p,
+                            C.c_void_p, C.c_void_p, P(thc_mps), P(thc_allocator), C.c_void_p],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -106,7 +108,7 @@ LIB = _load()
 EXPORTED = ("thc_apply_H", "thc_layer_apply", "thc_compress", "mps_inner", "mps_add_compress",
             "krylov_lanczos_ground", "krylov_expm_apply", "thc_kinetic_factors", "thc_mps_free",
             "thc_last_error", "thc_build_info", "thc_kernel_launches", "thc_profile_enable",
-            "thc_profile_read", "mps_inner_noalloc", "krylov_lanczos_restarted")
+            "thc_profile_read", "mps_inner_noalloc", "krylov_lanczos_restarted", "thc_expect_grad")
 
 
 # --------------------------------------------------------------------- allocator
@@ -312,6 +314,53 @@ def krylov_expm_apply(t, chi, zeta, psi, dt, K, D_max, tol=0.0, path="fp64"):
     _check(LIB.krylov_expm_apply(C.byref(h), C.byref(d), float(dt), int(K), C.byref(o), C.byref(out),
                                  C.byref(lost), C.byref(TORCH_ALLOCATOR), _stream()))
     return _take(out), lost.value
+
+
+def thc_expect_grad(t, chi, zeta, phi, psi, path="fp64", batch=0, grads=True):
+    """<phi|H|psi> (exact) and, with grads, (dE/dt, dE/dchi, dE/dzeta, dE/dpsi sites)."""
+    h = _ham(t, chi, zeta)
+    a, b = _desc(phi), _desc(psi)
+    o = _opts(1, 0.0, path, batch=batch)
+    v = C.c_double()
+    L, N = chi.shape
+    if grads:
+        dt = torch.empty(L, L, dtype=torch.float64, device=t.device)
+        dchi = torch.empty(L, N, dtype=torch.float64, device=t.device)
+        dz = torch.empty(N, N, dtype=torch.float64, device=t.device)
+        g = thc_mps()
+        _check(LIB.thc_expect_grad(C.byref(h), C.byref(a), C.byref(b), C.byref(o), C.byref(v), dt.data_ptr(),
+                                   dchi.data_ptr(), dz.data_ptr(), C.byref(g), C.byref(TORCH_ALLOCATOR), _stream()))
+        return v.value, dt, dchi, dz, _take(g)
+    _check(LIB.thc_expect_grad(C.byref(h), C.byref(a), C.byref(b), C.byref(o), C.byref(v), None, None, None, None,
+                               C.byref(TORCH_ALLOCATOR), _stream()))
+    return v.value
+
+
+class ThcExpectation(torch.autograd.Function):
+    """E = <phi|H(t, chi, zeta)|psi> as a differentiable function of t, chi,
+    zeta and the sites of psi (phi is held fixed).  The library computes E and
+    all of its derivatives in one pass of environment sweeps (thc_expect_grad);
+    backward scales them by the incoming gradient."""
+
+    @staticmethod
+    def forward(ctx, t, chi, zeta, n_phi, *sites):
+        phi, psi = list(sites[:n_phi]), list(sites[n_phi:])
+        path = "fp64" if psi[0].dtype == torch.float64 else "fp32"
+        v, dt, dchi, dz, dpsi = thc_expect_grad(t.detach(), chi.detach(), zeta.detach(),
+                                                [x.detach() for x in phi], [x.detach() for x in psi], path=path)
+        ctx.n_phi = n_phi
+        ctx.save_for_backward(dt, dchi, dz, *dpsi)
+        return torch.tensor(v, dtype=torch.float64, device=t.device)
+
+    @staticmethod
+    def backward(ctx, g):
+        dt, dchi, dz, *dpsi = ctx.saved_tensors
+        return (g * dt, g * dchi, g * dz, None, *([None] * ctx.n_phi), *[g.to(x.dtype) * x for x in dpsi])
+
+
+def expectation(t, chi, zeta, phi, psi):
+    """Differentiable <phi|H|psi> (see ThcExpectation)."""
+    return ThcExpectation.apply(t, chi, zeta, len(phi), *phi, *psi)
 
 
 def thc_kinetic_factors(t):

@@ -21,6 +21,8 @@ THC_ABI_FOR(extern template, c64)
 THC_ABI_FOR(extern template, c32)
 THC_ABI_FOR_EXPM(extern template, c64)
 THC_ABI_FOR_EXPM(extern template, c32)
+THC_ABI_FOR_REAL(extern template, double)
+THC_ABI_FOR_REAL(extern template, float)
 
 namespace {
 
@@ -238,6 +240,25 @@ thc_status krylov_lanczos_restarted(const thc_hamiltonian* H, const thc_mps* psi
             using T = std::remove_pointer_t<decltype(tag)>;
             return restarted_t<T>(H, psi0, K, cycles, n_lower, lower, opts, energies, state, alloc, stream);
         });
+    })
+}
+
+thc_status thc_expect_grad(const thc_hamiltonian* H, const thc_mps* phi, const thc_mps* psi, const thc_opts* opts,
+                           double* value, double* grad_t, double* grad_chi, double* grad_zeta, thc_mps* grad_psi,
+                           const thc_allocator* alloc, void* stream) {
+    THC_GUARD({
+        check_mps(phi, "phi");
+        check_mps(psi, "psi");
+        check_opts(opts);
+        check_ham(H, psi->L);
+        check_path_dtype(psi, opts);
+        if (phi->L != psi->L || phi->dtype != psi->dtype) throw Error(THC_EINVAL, "phi and psi differ in L or dtype");
+        if (is_complex(psi->dtype)) throw Error(THC_EUNSUPPORTED, "the adjoint is built for real MPS");
+        if (!value) throw Error(THC_EINVAL, "null value");
+        if (psi->dtype == THC_F64)
+            return expect_grad_t<double>(H, phi, psi, opts, value, grad_t, grad_chi, grad_zeta, grad_psi, alloc,
+                                         stream);
+        return expect_grad_t<float>(H, phi, psi, opts, value, grad_t, grad_chi, grad_zeta, grad_psi, alloc, stream);
     })
 }
 

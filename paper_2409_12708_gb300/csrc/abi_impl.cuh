@@ -279,6 +279,36 @@ thc_status restarted_t(const thc_hamiltonian* H, const thc_mps* psi0, int K, int
     return c.finish();
 }
 
+// Exact <phi|H|psi> and its derivatives (the adjoint): real MPS of the path's
+// precision.  grad_t / grad_chi / grad_zeta: device float64 arrays (written;
+// may be null); grad_psi: optional output MPS with psi's bonds and dtype.
+template <class T>
+thc_status expect_grad_t(const thc_hamiltonian* H, const thc_mps* phi, const thc_mps* psi, const thc_opts* o,
+                         double* value, double* grad_t, double* grad_chi, double* grad_zeta, thc_mps* grad_psi,
+                         const thc_allocator* a, void* stream) {
+    Call<T> c(stream, a, o);
+    const int L = psi->L, N = H->N;
+    const auto pa = bonds_of(phi), pb = bonds_of(psi);
+    T* pd = c.sc.template get<T>((size_t)Profile(pa).size);
+    T* qd = c.sc.template get<T>((size_t)Profile(pb).size);
+    c.ops.upload(phi, pa, pd);
+    c.ops.upload(psi, pb, qd);
+    double* vd = c.sc.template get<double>(1);
+    THC_CUDA(cudaMemsetAsync(vd, 0, sizeof(double), c.E.st));
+    if (grad_t) THC_CUDA(cudaMemsetAsync(grad_t, 0, sizeof(double) * L * L, c.E.st));
+    if (grad_chi) THC_CUDA(cudaMemsetAsync(grad_chi, 0, sizeof(double) * L * N, c.E.st));
+    if (grad_zeta) THC_CUDA(cudaMemsetAsync(grad_zeta, 0, sizeof(double) * N * N, c.E.st));
+    T* gd = nullptr;
+    if (grad_psi) {
+        gd = c.sc.template get<T>((size_t)Profile(pb).size);
+        THC_CUDA(cudaMemsetAsync(gd, 0, sizeof(T) * Profile(pb).size, c.E.st));
+    }
+    c.ops.expect_grad(H, pd, pa, qd, pb, o->batch, vd, grad_t, grad_chi, grad_zeta, gd);
+    THC_CUDA(cudaMemcpyAsync(value, vd, sizeof(double), cudaMemcpyDeviceToHost, c.E.st));
+    if (grad_psi) c.ops.download(gd, pb, grad_psi, psi->dtype);
+    return c.finish();
+}
+
 // One global-Krylov time step (Sec. 2.2, Eq. Krylov_combination) on complex
 // site tensors T: K vectors from psi/|psi|, the projected problem with
 // a(dt) = exp(-i dt Heff) a(0) in the orthonormalised basis, the combination
@@ -347,6 +377,10 @@ thc_status expm_t(const thc_hamiltonian* H, const thc_mps* psi, double dt, int K
     PREFIX thc_status thc::abi::restarted_t<T>(const thc_hamiltonian*, const thc_mps*, int, int, int,           \
                                                const thc_mps* const*, const thc_opts*, double*, thc_mps*,        \
                                                const thc_allocator*, void*);
+#define THC_ABI_FOR_REAL(PREFIX, T)                                                                             \
+    PREFIX thc_status thc::abi::expect_grad_t<T>(const thc_hamiltonian*, const thc_mps*, const thc_mps*,         \
+                                                 const thc_opts*, double*, double*, double*, double*, thc_mps*,  \
+                                                 const thc_allocator*, void*);
 #define THC_ABI_FOR_EXPM(PREFIX, T)                                                                             \
     PREFIX thc_status thc::abi::expm_t<T>(const thc_hamiltonian*, const thc_mps*, double, int, const thc_opts*,  \
                                           thc_mps*, double*, const thc_allocator*, void*);

@@ -98,6 +98,11 @@ struct Engine {
                 dim3 grid(ceil_div(N, tc::BN), ceil_div(M, tc::BM), batch);
                 k_gemm_tc<LA, LB, SC><<<grid, tc::THREADS, tc::SMEM, st>>>(M, N, K, la, lb, sc, dflag);
                 THC_CUDA(cudaGetLastError());
+                Profiler& p = profiler();
+                if (p.on) {  // how many contractions ran on the tensor cores
+                    std::lock_guard<std::mutex> g(p.mu);
+                    p.acc["tc_gemm_launches"].first += 1;
+                }
                 return;
             }
         }

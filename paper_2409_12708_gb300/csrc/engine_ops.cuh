@@ -4,6 +4,7 @@
 #include <cmath>
 
 #include "engine_impl.cuh"
+#include "adjoint.cuh"
 
 namespace thc {
 
@@ -66,6 +67,16 @@ __global__ void k_scale(T* x, long n, typename Wide<T>::type c) {
 }
 
 static __global__ void k_set_int(int* p, int v) { *p = v; }
+
+template <class T>
+struct AdjTransA {  // A(m, k) = base_b[k*ld + m] (transposed access, real)
+    const T* base;
+    long stride;
+    int ld;
+    __device__ __forceinline__ T operator()(int b, int m, int k) const {
+        return base[(long)b * stride + (long)k * ld + m];
+    }
+};
 
 static __global__ void k_pack_complex(c64* out, const double* re, const double* im, int n) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) out[i] = c64{re[i], im[i]};
@@ -443,6 +454,142 @@ struct Ops {
             for (int j = 0; j < nv; ++j) S[(size_t)j * nv + k] = tmp[j];
         }
         return nv;
+    }
+
+    // ------------------------------------------------------------- adjoint
+    // value = <phi|H|psi> (exact, no compression) and, where the pointers are
+    // given, dE/dt [L*L], dE/dchi [L*N], dE/dzeta [N*N] (device float64, added
+    // to) and dE/dpsi (device, psi's profile, added to).  phi, psi: device MPS
+    // in the contiguous layout with profiles pa, pb.  Real T only.
+    void expect_grad(const thc_hamiltonian* H, const T* phi, const std::vector<int>& pa, const T* psi,
+                     const std::vector<int>& pb, int batch, double* value_dev, double* dt, double* dchi,
+                     double* dzeta, T* dpsi) {
+        static_assert(!is_complex_v<T>, "the adjoint is built for real MPS");
+        const int L = H->L, N = H->N;
+        Profile A(pa), Bp(pb);
+        for (int kind = 0; kind < 2; ++kind) {
+            const int NL = kind == 0 ? 2 : 4, NW = 1 << NL;
+            const long nterms = kind == 0 ? 2L * L : 4L * N * N;
+            // per-term scratch: all left environments, one site's X / Q / P, two R, G
+            long envTot = 0, blk = 0, rmax = 0, gmax = 0;
+            std::vector<long> eoff(L + 1);
+            for (int s = 0; s <= L; ++s) {
+                eoff[s] = envTot;
+                envTot += (long)pa[s] * NW * pb[s];
+                rmax = std::max(rmax, (long)pa[s] * NW * pb[s]);
+            }
+            for (int s = 0; s < L; ++s) {
+                blk = std::max(blk, (long)pa[s] * NW * 4 * pb[s + 1]);
+                gmax = std::max(gmax, (long)pb[s] * 4 * pb[s + 1]);
+            }
+            const size_t per_term = sizeof(T) * (size_t)(envTot + 3 * blk + 2 * rmax + gmax) +
+                                    sizeof(double) * (size_t)(NL * L + 2) + sizeof(T) * (size_t)(NL * L) + 64;
+            size_t freeb = 0, totalb = 0;
+            THC_CUDA(cudaMemGetInfo(&freeb, &totalb));
+            long Bw = batch > 0 ? batch : 4L * E.sms;
+            Bw = std::max(1L, std::min<long>({Bw, nterms, (long)(0.4 * freeb / per_term)}));
+            Scratch sc(E.al);
+            T* Eall = sc.get<T>((size_t)Bw * envTot);
+            T* X = sc.get<T>((size_t)Bw * blk);
+            T* QY = sc.get<T>((size_t)Bw * blk);
+            T* P = sc.get<T>((size_t)Bw * blk);
+            T* R[2] = {sc.get<T>((size_t)Bw * rmax), sc.get<T>((size_t)Bw * rmax)};
+            T* G = dpsi ? sc.get<T>((size_t)Bw * gmax) : nullptr;
+            int* op = sc.get<int>((size_t)Bw * NL);
+            T* coef = sc.get<T>((size_t)Bw * NL * L);
+            double* weight = sc.get<double>((size_t)Bw);
+            double* val = sc.get<double>((size_t)Bw);
+            double* g = sc.get<double>((size_t)Bw * NL * L);
+            const AdjTerms<T> tm{op, coef, NL, L};
+            for (long t0 = 0; t0 < nterms; t0 += Bw) {
+                const int Bc = (int)std::min<long>(Bw, nterms - t0);
+                {
+                    THC_LAUNCH("adj_terms", st());
+                    k_adj_terms<T><<<Bc, 32, 0, st()>>>(kind, t0, Bc, L, N, H->t, H->chi, H->zeta, op, coef, weight);
+                }
+                E.check();
+                THC_CUDA(cudaMemsetAsync(g, 0, sizeof(double) * (size_t)Bc * NL * L, st()));
+                {
+                    THC_LAUNCH("adj_terms", st());
+                    k_adj_boundary<T><<<ceil_div(Bc, 128), 128, 0, st()>>>(Bc, Eall, envTot, R[L & 1], rmax, NW);
+                }
+                E.check();
+                // ---- left sweep: X = E_s psi_s, Y = M_s X, E_{s+1} = phi_s^T Y
+                for (int s = 0; s < L; ++s) {
+                    const int Da = pa[s], Dap = pa[s + 1], Db = pb[s], Dbp = pb[s + 1];
+                    {
+                        THC_LAUNCH("adj_gemm", st());
+                        E.gemm(Bc, Da * NW, 4 * Dbp, Db, RowMajorA<T>{Eall + eoff[s], envTot, Db},
+                               RowMajorB<T>{psi + Bp.off[s], 0, 4 * Dbp}, StoreRM<T>{X, blk, 4 * Dbp});
+                    }
+                    {
+                        THC_LAUNCH("adj_layers", st());
+                        dim3 grd(ceil_div(Da * Dbp, 256), Bc);
+                        if (NL == 2) k_adj_fwd<T, 2><<<grd, 256, 0, st()>>>(Da, Dbp, blk, X, QY, tm, s);
+                        else k_adj_fwd<T, 4><<<grd, 256, 0, st()>>>(Da, Dbp, blk, X, QY, tm, s);
+                    }
+                    E.check();
+                    {
+                        THC_LAUNCH("adj_gemm", st());
+                        E.gemm(Bc, Dap, NW * Dbp, 4 * Da, AdjTransA<T>{phi + A.off[s], 0, Dap},
+                               RowMajorB<T>{QY, blk, NW * Dbp}, StoreRM<T>{Eall + eoff[s + 1], envTot, NW * Dbp});
+                    }
+                }
+                {
+                    THC_LAUNCH("adj_terms", st());
+                    k_adj_values<T><<<ceil_div(Bc, 128), 128, 0, st()>>>(Bc, Eall + eoff[L], envTot, NW, val);
+                }
+                E.check();
+                // ---- right sweep: Q = phi_s R_{s+1}, P = M_s^T Q (+ coefficient
+                // gradients against X = E_s psi_s), R_s = P psi_s^T, G = E_s^T P
+                // (skipped when only the value is asked for)
+                const bool grads = dt || dchi || dzeta || dpsi;
+                for (int s = L - 1; s >= 0 && grads; --s) {
+                    const int Da = pa[s], Dap = pa[s + 1], Db = pb[s], Dbp = pb[s + 1];
+                    T* Rn = R[(s + 1) & 1];
+                    T* Rc = R[s & 1];
+                    {
+                        THC_LAUNCH("adj_gemm", st());
+                        E.gemm(Bc, 4 * Da, NW * Dbp, Dap, RowMajorA<T>{phi + A.off[s], 0, Dap},
+                               RowMajorB<T>{Rn, rmax, NW * Dbp}, StoreRM<T>{QY, blk, NW * Dbp});
+                    }
+                    {
+                        THC_LAUNCH("adj_gemm", st());
+                        E.gemm(Bc, Da * NW, 4 * Dbp, Db, RowMajorA<T>{Eall + eoff[s], envTot, Db},
+                               RowMajorB<T>{psi + Bp.off[s], 0, 4 * Dbp}, StoreRM<T>{X, blk, 4 * Dbp});
+                    }
+                    {
+                        THC_LAUNCH("adj_layers", st());
+                        dim3 grd(ceil_div(Da * Dbp, 256), Bc);
+                        if (NL == 2) k_adj_bwd<T, 2><<<grd, 256, 0, st()>>>(Da, Dbp, blk, QY, P, X, g, tm, s);
+                        else k_adj_bwd<T, 4><<<grd, 256, 0, st()>>>(Da, Dbp, blk, QY, P, X, g, tm, s);
+                    }
+                    E.check();
+                    if (s > 0) {
+                        THC_LAUNCH("adj_gemm", st());
+                        E.gemm(Bc, Da * NW, Db, 4 * Dbp, RowMajorA<T>{P, blk, 4 * Dbp},
+                               TransB<T>{psi + Bp.off[s], 0, 4 * Dbp}, StoreRM<T>{Rc, rmax, Db});
+                    }
+                    if (dpsi) {
+                        {
+                            THC_LAUNCH("adj_gemm", st());
+                            E.gemm(Bc, Db, 4 * Dbp, Da * NW, AdjTransA<T>{Eall + eoff[s], envTot, Db},
+                                   RowMajorB<T>{P, blk, 4 * Dbp}, StoreRM<T>{G, gmax, 4 * Dbp});
+                        }
+                        const long n = (long)Db * 4 * Dbp;
+                        THC_LAUNCH("adj_accum", st());
+                        k_adj_accum_site<T><<<std::max(1, (int)std::min<long>(ceil_div((int)std::min<long>(n, 1L << 30), 256), 1024)),
+                                              256, 0, st()>>>(Bc, G, gmax, n, weight, dpsi + Bp.off[s]);
+                        E.check();
+                    }
+                }
+                {
+                    THC_LAUNCH("adj_accum", st());
+                    k_adj_params<<<Bc, 32, 0, st()>>>(kind, t0, Bc, L, N, val, g, weight, value_dev, dt, dchi, dzeta);
+                }
+                E.check();
+            }
+        }
     }
 
     // projected problem on the device (float64 single-CTA kernel; the complex

@@ -5,3 +5,4 @@ using thc::c32;
 using thc::c64;
 
 THC_ABI_FOR(template, float)
+THC_ABI_FOR_REAL(template, float)

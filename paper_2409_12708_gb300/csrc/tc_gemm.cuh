@@ -1,23 +1,32 @@
 // tc_gemm.cuh -- batched float32 GEMM on the 5th-generation tensor cores
-// (tcgen05.mma kind::tf32, accumulator in tensor memory), with the error-
+// (tcgen05.mma kind::tf32, accumulators in tensor memory), with the error-
 // compensated split of Ootomo & Yokota (2022): each float32 operand is the sum
 // of two TF32 numbers, a = a_hi + a_lo, and C = A_hi B_hi + A_hi B_lo + A_lo B_hi
-// accumulated in float32 reaches float32 accuracy (the dropped A_lo B_lo term
-// is ~2^-22 of the product).
+// reaches float32 accuracy (the dropped A_lo B_lo term is ~2^-22 of the
+// product).  The tensor core adds into its float32 accumulator with rounding
+// toward zero; accumulated over a whole K that bias shrinks every product by
+// ~K ulps, and a compression chains enough products for it to show (measured:
+// -4e-4 in |H psi|^2 over 16 terms).  So, as in that paper, accumulation across
+// K happens outside the tensor core: every 32-wide K slice is accumulated in a
+// fresh pair of tensor-memory accumulators (A_hi B_hi, and the two correction
+// products), which the threads read back and add into float32 registers with
+// round-to-nearest.
 //
 // C[b](m, n) = sum_k A[b](m, k) B[b](k, n), operands produced element by
 // element by loader functors (the bond-2 MPO expansion and the direct sum stay
 // fused into the operand load), C written by a store functor.  One CTA of 256
 // threads per 128 x 128 tile of C (blockIdx.z = batch):
-//   * every thread loads and splits the 128 x 32 slices of A and B^T into
-//     shared memory in the no-swizzle K-major canonical layout (8-row x 16-byte
-//     core matrices; k-chunks 128 bytes apart, 8-row groups 1 KB apart), two
-//     stages, so the loads of slice k+1 overlap the MMAs of slice k;
-//   * one thread issues the 12 MMAs of a slice (K = 8 each, three products) and
-//     commits them to the stage's mbarrier;
-//   * the 128 x 128 float32 accumulator lives in 128 columns of tensor memory;
-//     the epilogue reads it with tcgen05.ld (warp w: lanes 32 (w % 4) ..,
-//     columns 64 (w / 4) ..).
+//   * the threads load the 128 x 32 slices of A and B^T into registers (each
+//     thread 4 rows' 4-element k-chunks of each), split them, and store them in
+//     the no-swizzle K-major canonical layout (8-row x 16-byte core matrices;
+//     k-chunks 128 bytes apart, 8-row groups 1 KB apart) with 16-byte stores
+//     that fill 512 contiguous bytes per warp; two stages;
+//   * one thread issues the 12 MMAs of a slice (K = 8 each) into the slice's
+//     accumulator pair and commits them to the stage's mbarrier;
+//   * while the tensor core works on slice k, the threads read back slice
+//     k-1's accumulators (tcgen05.ld; warp w: lanes 32 (w % 4) .., columns
+//     64 (w / 4) ..) and add them to their registers; the pairs alternate, so
+//     tensor memory holds 4 x 128 columns.
 // Waits on an mbarrier are bounded (one second by %globaltimer); a wait that
 // gives up sets DEV_TC_TIMEOUT in the status word, skips the epilogue, and the
 // CTA still releases its tensor memory before it returns.
@@ -41,7 +50,7 @@ constexpr int SMEM = 2 * STAGE + 1024;     // two stages + alignment slack
 // instruction descriptor: float32 accumulator, TF32 A and B, both K-major, N = 128, M = 128
 constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
                            ((uint32_t)(BM >> 4) << 24);
-constexpr uint32_t TMEM_COLS = 128;
+constexpr uint32_t TMEM_COLS = 512;  // 2 slices in flight x (hi product, corrections) x 128 columns
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -115,7 +124,7 @@ k_gemm_tc(int M, int N, int K, LA la, LB lb, SC sc, int* status) {
                                                            ~(uintptr_t)1023);
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tmem_sh;
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int b = blockIdx.z, m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_sh)),
@@ -132,6 +141,15 @@ k_gemm_tc(int M, int N, int K, LA la, LB lb, SC sc, int* status) {
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_sh;
     const int nkt = (K + BK - 1) / BK;
+    // this thread's share of the accumulator: row lane_base + lane, 64 columns
+    const int lane_base = 32 * (warp & 3), col_base = 64 * (warp >> 2);
+    float acc[64];
+#pragma unroll
+    for (int j = 0; j < 64; ++j) acc[j] = 0.f;
+    // loads: lane -> (row (lane & 7) of an 8-row group, k-chunk (lane >> 3) of a quad);
+    // warp w, step j -> 8-row group 2 j + (w >> 2) ... so the 8 warps x 4 steps cover
+    // 16 row groups x 2 chunk quads
+    const int lr = lane & 7, lc = lane >> 3;
     uint32_t parity[2] = {0u, 0u};
     bool ok = true;
     for (int kt = 0; kt < nkt && ok; ++kt) {
@@ -140,36 +158,48 @@ k_gemm_tc(int M, int N, int K, LA la, LB lb, SC sc, int* status) {
         unsigned char* a_lo = a_hi + PART;
         unsigned char* b_hi = a_hi + 2 * PART;
         unsigned char* b_lo = a_hi + 3 * PART;
-        if (kt >= 2) {  // the MMAs of slice kt-2 read this stage
-            // the decision is made uniform across the CTA (barriers follow)
-            ok = __syncthreads_and(mbar_wait(smem_u32(&mbar[st]), parity[st]) ? 1 : 0) != 0;
-            parity[st] ^= 1u;
-            if (!ok) {
-                if (tid == 0) atomicOr(status, DEV_TC_TIMEOUT);
-                break;
+        const int k0 = kt * BK;
+        float va[4][4], vb[4][4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int unit = warp * 4 + j;            // 0..31
+            const int g = unit >> 1, q = unit & 1;    // row group, chunk quad
+            const int r = g * 8 + lr, c = q * 4 + lc; // row in tile, k-chunk in slice
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int k = k0 + 4 * c + e;
+                va[j][e] = (m0 + r < M && k < K) ? (float)la(b, m0 + r, k) : 0.f;
+                vb[j][e] = (n0 + r < N && k < K) ? (float)lb(b, k, n0 + r) : 0.f;
             }
         }
-        const int k0 = kt * BK;
-        // A slice: consecutive threads walk k (row-major A is contiguous in k)
-        for (int i = tid; i < BM * BK; i += THREADS) {
-            const int r = i / BK, k = i % BK;
-            const float a = (m0 + r < M && k0 + k < K) ? (float)la(b, m0 + r, k0 + k) : 0.f;
-            const uint32_t h = tf32_rna(a);
-            const uint32_t l = tf32_rna(a - __uint_as_float(h));
-            *reinterpret_cast<uint32_t*>(a_hi + kmaj_off(r, k)) = h;
-            *reinterpret_cast<uint32_t*>(a_lo + kmaj_off(r, k)) = l;
-        }
-        // B^T slice: consecutive threads walk n (row-major B is contiguous in n)
-        for (int i = tid; i < BN * BK; i += THREADS) {
-            const int k = i / BN, r = i % BN;
-            const float v = (n0 + r < N && k0 + k < K) ? (float)lb(b, k0 + k, n0 + r) : 0.f;
-            const uint32_t h = tf32_rna(v);
-            const uint32_t l = tf32_rna(v - __uint_as_float(h));
-            *reinterpret_cast<uint32_t*>(b_hi + kmaj_off(r, k)) = h;
-            *reinterpret_cast<uint32_t*>(b_lo + kmaj_off(r, k)) = l;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int unit = warp * 4 + j;
+            const int g = unit >> 1, q = unit & 1;
+            const int r = g * 8 + lr, c = q * 4 + lc;
+            const uint32_t off = kmaj_off(r, 4 * c);
+            uint4 ah, al, bh, bl;
+            uint32_t* pah = reinterpret_cast<uint32_t*>(&ah);
+            uint32_t* pal = reinterpret_cast<uint32_t*>(&al);
+            uint32_t* pbh = reinterpret_cast<uint32_t*>(&bh);
+            uint32_t* pbl = reinterpret_cast<uint32_t*>(&bl);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                pah[e] = tf32_rna(va[j][e]);
+                pal[e] = tf32_rna(va[j][e] - __uint_as_float(pah[e]));
+                pbh[e] = tf32_rna(vb[j][e]);
+                pbl[e] = tf32_rna(vb[j][e] - __uint_as_float(pbh[e]));
+            }
+            *reinterpret_cast<uint4*>(a_hi + off) = ah;
+            *reinterpret_cast<uint4*>(a_lo + off) = al;
+            *reinterpret_cast<uint4*>(b_hi + off) = bh;
+            *reinterpret_cast<uint4*>(b_lo + off) = bl;
         }
         asm volatile("fence.proxy.async.shared::cta;");
         __syncthreads();
+        // slice kt: hi product into columns 256 st + [0, 128), corrections into
+        // 256 st + [128, 256), both started fresh
+        const uint32_t t_hi = tmem + 256u * (uint32_t)st, t_co = t_hi + 128u;
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
@@ -177,39 +207,65 @@ k_gemm_tc(int M, int N, int K, LA la, LB lb, SC sc, int* status) {
                 const uint32_t off = (uint32_t)(kk >> 2) * LBO;
                 const uint64_t dah = desc(smem_u32(a_hi) + off), dal = desc(smem_u32(a_lo) + off);
                 const uint64_t dbh = desc(smem_u32(b_hi) + off), dbl = desc(smem_u32(b_lo) + off);
-                mma_tf32(tmem, dah, dbh, (kt > 0 || kk > 0) ? 1u : 0u);
-                mma_tf32(tmem, dah, dbl, 1u);
-                mma_tf32(tmem, dal, dbh, 1u);
+                mma_tf32(t_hi, dah, dbh, kk > 0 ? 1u : 0u);
+                mma_tf32(t_co, dah, dbl, kk > 0 ? 1u : 0u);
+                mma_tf32(t_co, dal, dbh, 1u);
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                 smem_u32(&mbar[st])));
         }
-    }
-    // the last one or two slices' MMAs
-    if (ok) {
-        for (int s = 0; s < 2 && ok; ++s) {
-            const int kt = nkt - 1 - s;
-            if (kt < 0) break;
-            const int st = kt & 1;
-            ok = __syncthreads_and(mbar_wait(smem_u32(&mbar[st]), parity[st]) ? 1 : 0) != 0;
-            if (!ok && tid == 0) atomicOr(status, DEV_TC_TIMEOUT);
+        // fold slice kt-1 into the registers while the tensor core runs slice kt
+        // (the wait also frees stage kt-1's shared memory for slice kt+1)
+        if (kt >= 1) {
+            const int sp = st ^ 1;
+            ok = __syncthreads_and(mbar_wait(smem_u32(&mbar[sp]), parity[sp]) ? 1 : 0) != 0;
+            parity[sp] ^= 1u;
+            if (!ok) {
+                if (tid == 0) atomicOr(status, DEV_TC_TIMEOUT);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t p_hi = tmem + 256u * (uint32_t)sp + ((uint32_t)lane_base << 16) + (uint32_t)col_base;
+#pragma unroll
+            for (int c = 0; c < 64; c += 32) {
+                uint32_t vh[32], vc[32];
+                ld32<0>(p_hi + (uint32_t)c, vh);
+                ld32<1>(p_hi + 128u + (uint32_t)c, vc);
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+                for (int j = 0; j < 32; ++j) acc[c + j] += __uint_as_float(vh[j]) + __uint_as_float(vc[j]);
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncthreads();  // accumulator pair sp is read: slice kt+1 may overwrite it
         }
     }
-    asm volatile("tcgen05.fence::after_thread_sync;");
+    // the last slice
     if (ok && nkt > 0) {
-        const int lane_base = 32 * (warp & 3), col_base = 64 * (warp >> 2);
-        const int m = m0 + lane_base + (tid & 31);
+        const int sp = (nkt - 1) & 1;
+        ok = __syncthreads_and(mbar_wait(smem_u32(&mbar[sp]), parity[sp]) ? 1 : 0) != 0;
+        if (!ok) {
+            if (tid == 0) atomicOr(status, DEV_TC_TIMEOUT);
+        } else {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t p_hi = tmem + 256u * (uint32_t)sp + ((uint32_t)lane_base << 16) + (uint32_t)col_base;
 #pragma unroll
-        for (int c = 0; c < 64; c += 32) {
-            uint32_t v[32];
-            ld32<0>(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(col_base + c), v);
-            asm volatile("tcgen05.wait::ld.sync.aligned;");
-            if (m < M) {
+            for (int c = 0; c < 64; c += 32) {
+                uint32_t vh[32], vc[32];
+                ld32<0>(p_hi + (uint32_t)c, vh);
+                ld32<1>(p_hi + 128u + (uint32_t)c, vc);
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int n = n0 + col_base + c + j;
-                    if (n < N) sc(b, m, n, __uint_as_float(v[j]));
-                }
+                for (int j = 0; j < 32; ++j) acc[c + j] += __uint_as_float(vh[j]) + __uint_as_float(vc[j]);
+            }
+        }
+    }
+    if (ok) {
+        const int m = m0 + lane_base + lane;
+        if (m < M) {
+#pragma unroll
+            for (int j = 0; j < 64; ++j) {
+                const int n = n0 + col_base + j;
+                if (n < N) sc(b, m, n, acc[j]);
             }
         }
     }
