@@ -28,7 +28,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_2409_12708_gb300.workloads import WORKLOADS, full_bond_profile, workload  # noqa: E402
+from paper_2409_12708_gb300.workloads import (WORKLOADS, full_bond_profile, sector_mps,  # noqa: E402
+                                              thc_hamiltonian, workload)
 
 METRIC = ("THC terms/s and H|ψ⟩ applies/s; Krylov step time, batched+mixed vs plain FP64")
 WORKLOAD = "L16_N48_D128"
@@ -50,12 +51,15 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--batch", type=int, default=0)
-    p.add_argument("--path", default="fp32", choices=["fp32", "tf32"],
+    p.add_argument("--path", default="tf32", choices=["fp32", "tf32"],
                    help="compute path of the headline (tf32: contractions on the tensor cores)")
     p.add_argument("--terms", type=int, default=0,
                    help="apply only the first TERMS terms per step (0 = all; for profiling slices)")
     p.add_argument("--no-profile", action="store_true", help="skip the CUDA-event profiled step")
     p.add_argument("--no-krylov", action="store_true", help="skip the Lanczos step timing")
+    p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (L=16, N=48, D=64) record")
+    p.add_argument("--no-expm", action="store_true", help="skip the Krylov time-step record")
+    p.add_argument("--no-config2", action="store_true", help="skip the L=24, N=96, D=256 slice record")
     return p.parse_args()
 
 
@@ -480,6 +484,107 @@ def run_ours(args):
                     rec["minus_dense_lanczos_K10"] = en - gold["dense_lanczos_K10"]
                 krylov[f"{pth}_D{Dx}"] = rec
 
+    # ---- the adjoint on the L=16, N=48, D_max=64 configuration: phi and psi
+    # independent half-filled states; all 9248 terms in float32 (value and every
+    # derivative), the float64 path on one (nu, s') block (96 terms,
+    # extrapolated, labelled), and central finite differences (step 1e-5) of
+    # that block's float64 value on random entries of chi, zeta and psi
+    adjoint = None
+    if not args.no_adjoint and rank == 0:
+        tA, cA, zA = thc_hamiltonian(16, 48, seed=0)
+        phiA = sector_mps(16, 8, 8, 64, seed=1003)
+        psiA = sector_mps(16, 8, 8, 64, seed=1013)
+        HA = (dev(tA), dev(cA), dev(zA))
+        TA = 4 * 48 * 48 + 32
+        adjoint = {"workload": "L16_N48_D64 (phi, psi independent half-filled)", "terms": TA}
+        p32 = ([dev(a, torch.float32) for a in phiA], [dev(a, torch.float32) for a in psiA])
+        p64 = ([dev(a) for a in phiA], [dev(a) for a in psiA])
+        B.thc_expect_grad(*HA, *p32, path="fp32", term_begin=0, term_end=96)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        v32 = B.thc_expect_grad(*HA, *p32, path="fp32")
+        e1.record()
+        e1.synchronize()
+        adjoint["fp32_all_terms_s"] = e0.elapsed_time(e1) / 1e3
+        adjoint["fp32_value"] = v32[0]
+        e0.record()
+        v64 = B.thc_expect_grad(*HA, *p64, term_begin=0, term_end=96)
+        e1.record()
+        e1.synchronize()
+        s64 = e0.elapsed_time(e1) / 1e3
+        adjoint["fp64_96_terms_s"] = s64
+        adjoint["fp64_extrapolated_all_terms_s"] = s64 * TA / 96
+        rng = np.random.default_rng(7)
+        worst = 0.0
+        X, Z, P = HA[1], HA[2], p64[1]
+        val = lambda x, z, pp: B.thc_expect_grad(HA[0], x, z, p64[0], pp, grads=False, term_begin=0, term_end=96)
+        for _ in range(4):
+            for which in ("chi", "zeta", "psi"):
+                if which == "chi":
+                    i = (int(rng.integers(16)), int(rng.integers(48)))
+                    xp, xm = X.clone(), X.clone()
+                    xp[i] += 1e-5
+                    xm[i] -= 1e-5
+                    fd = (val(xp, Z, P) - val(xm, Z, P)) / 2e-5
+                    g = float(v64[2][i])
+                elif which == "zeta":
+                    i = (int(rng.integers(48)), int(rng.integers(48)))
+                    zp, zm = Z.clone(), Z.clone()
+                    zp[i] += 1e-5
+                    zm[i] -= 1e-5
+                    fd = (val(X, zp, P) - val(X, zm, P)) / 2e-5
+                    g = float(v64[3][i])
+                else:
+                    st = int(rng.integers(16))
+                    i = tuple(int(rng.integers(n)) for n in P[st].shape)
+                    pp, pm = [x.clone() for x in P], [x.clone() for x in P]
+                    pp[st][i] += 1e-5
+                    pm[st][i] -= 1e-5
+                    fd = (val(X, Z, pp) - val(X, Z, pm)) / 2e-5
+                    g = float(v64[4][st][i])
+                worst = max(worst, abs(g - fd) / max(abs(fd), 1e-2))
+        adjoint["fp64_fd_check"] = {"entries": 12, "step": 1e-5, "max_rel_error": worst,
+                                    "note": "terms [0,96), float64, central differences"}
+
+    # ---- one Krylov time step (K = 12, dt = 0.05) with complex site tensors
+    expm = None
+    if not args.no_expm and rank == 0:
+        tk, ck, zk, pk, Dk = workload("L6_N12_D16")
+        Hk = (dev(tk), dev(ck), dev(zk))
+        expm = {"workload": "L6_N12_D16", "K": 12, "dt": 0.05}
+        for pth, dtk in (("fp64", torch.float64), ("fp32", torch.float32)):
+            pp = [dev(a, dtk) for a in pk]
+            B.krylov_expm_apply(*Hk, pp, 0.05, 12, Dk, path=pth)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _, lost = B.krylov_expm_apply(*Hk, pp, 0.05, 12, Dk, path=pth)
+            e1.record()
+            e1.synchronize()
+            expm[pth] = {"s_per_time_step": e0.elapsed_time(e1) / 1e3, "lost_norm": lost}
+
+    # ---- the L=24, N=96, D_max=256 configuration on one (nu, s') block
+    # (192 terms), extrapolated to a full H|psi> and a 20-step Lanczos (labelled)
+    config2 = None
+    if not args.no_config2 and rank == 0:
+        t2, c2, z2, p2, D2 = workload("L24_N96_D256")
+        H2 = (dev(t2), dev(c2), dev(z2))
+        T2 = 4 * 96 * 96 + 48
+        config2 = {"workload": "L24_N96_D256", "terms": T2, "timed_terms": 192}
+        pp = [dev(a, torch.float32) for a in p2]
+        B.thc_apply_H(*H2, pp, D_max=D2, path=args.path, term_begin=0, term_end=8, batch=8)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        B.thc_apply_H(*H2, pp, D_max=D2, path=args.path, term_begin=0, term_end=192)
+        e1.record()
+        e1.synchronize()
+        s2 = e0.elapsed_time(e1) / 1e3
+        config2.update({"path": args.path, "terms_per_s": 192 / s2, "extrapolated_hpsi_s": s2 * T2 / 192,
+                        "extrapolated_20_step_lanczos_s": 20 * s2 * T2 / 192,
+                        "note": "one (nu, s') block timed, whole H|psi> and Lanczos extrapolated"})
+
     if rank != 0:
         return
     clocks = clk.summary()
@@ -508,6 +613,9 @@ def run_ours(args):
                                   if k.startswith("jacobi_sweeps")},
         "compressions_per_step": n_compress,
         "krylov": krylov,
+        "adjoint": adjoint,
+        "expm": expm,
+        "config2": config2,
     }
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(args)

@@ -228,8 +228,10 @@ thc_status krylov_expm_apply(const thc_hamiltonian* H, const thc_mps* psi, doubl
  *    (every entry an independent variable); each may be NULL.
  *  - grad_psi: optional output MPS (psi's bonds and dtype), site i =
  *    dE/d(site i of psi); NULL to skip.
- *  - opts: path and batch (terms in flight) are used; D_max and tol are not
- *    (nothing is truncated).
+ *  - opts: path, batch (terms in flight) and the term range (thc_apply_H's
+ *    term indexing; the value and derivatives are then those of the sum of
+ *    the terms in range) are used; D_max and tol are not (nothing is
+ *    truncated).
  * Errors: THC_EINVAL, THC_EUNSUPPORTED (complex MPS), THC_ENOMEM, THC_ECUDA. */
 thc_status thc_expect_grad(const thc_hamiltonian* H, const thc_mps* phi, const thc_mps* psi,
                            const thc_opts* opts, double* value, double* grad_t, double* grad_chi,

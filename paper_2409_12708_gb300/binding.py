@@ -316,11 +316,12 @@ def krylov_expm_apply(t, chi, zeta, psi, dt, K, D_max, tol=0.0, path="fp64"):
     return _take(out), lost.value
 
 
-def thc_expect_grad(t, chi, zeta, phi, psi, path="fp64", batch=0, grads=True):
-    """<phi|H|psi> (exact) and, with grads, (dE/dt, dE/dchi, dE/dzeta, dE/dpsi sites)."""
+def thc_expect_grad(t, chi, zeta, phi, psi, path="fp64", batch=0, grads=True, term_begin=-1, term_end=-1):
+    """<phi|H|psi> (exact) and, with grads, (dE/dt, dE/dchi, dE/dzeta, dE/dpsi sites);
+    with a term range, of the sum of those terms only."""
     h = _ham(t, chi, zeta)
     a, b = _desc(phi), _desc(psi)
-    o = _opts(1, 0.0, path, batch=batch)
+    o = _opts(1, 0.0, path, term_begin, term_end, batch=batch)
     v = C.c_double()
     L, N = chi.shape
     if grads:

@@ -303,7 +303,7 @@ thc_status expect_grad_t(const thc_hamiltonian* H, const thc_mps* phi, const thc
         gd = c.sc.template get<T>((size_t)Profile(pb).size);
         THC_CUDA(cudaMemsetAsync(gd, 0, sizeof(T) * Profile(pb).size, c.E.st));
     }
-    c.ops.expect_grad(H, pd, pa, qd, pb, o->batch, vd, grad_t, grad_chi, grad_zeta, gd);
+    c.ops.expect_grad(H, pd, pa, qd, pb, o->batch, o->term_begin, o->term_end, vd, grad_t, grad_chi, grad_zeta, gd);
     THC_CUDA(cudaMemcpyAsync(value, vd, sizeof(double), cudaMemcpyDeviceToHost, c.E.st));
     if (grad_psi) c.ops.download(gd, pb, grad_psi, psi->dtype);
     return c.finish();

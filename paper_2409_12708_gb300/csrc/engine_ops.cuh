@@ -462,14 +462,22 @@ struct Ops {
     // to) and dE/dpsi (device, psi's profile, added to).  phi, psi: device MPS
     // in the contiguous layout with profiles pa, pb.  Real T only.
     void expect_grad(const thc_hamiltonian* H, const T* phi, const std::vector<int>& pa, const T* psi,
-                     const std::vector<int>& pb, int batch, double* value_dev, double* dt, double* dchi,
-                     double* dzeta, T* dpsi) {
+                     const std::vector<int>& pb, int batch, long term_begin, long term_end, double* value_dev,
+                     double* dt, double* dchi, double* dzeta, T* dpsi) {
         static_assert(!is_complex_v<T>, "the adjoint is built for real MPS");
         const int L = H->L, N = H->N;
         Profile A(pa), Bp(pb);
+        // the term range in thc_apply_H's indexing: Coulomb [0, 4N^2), one-body after
+        const long VV = 4L * N * N, TT = VV + 2L * L;
+        const long r0 = term_begin < 0 ? 0 : term_begin, r1 = term_end < 0 ? TT : std::min(TT, term_end);
+        if (r1 <= r0) throw Error(THC_EINVAL, "empty term range");
         for (int kind = 0; kind < 2; ++kind) {
             const int NL = kind == 0 ? 2 : 4, NW = 1 << NL;
-            const long nterms = kind == 0 ? 2L * L : 4L * N * N;
+            // this kind's terms [first, last) in its own numbering
+            const long base = kind == 0 ? VV : 0, count = kind == 0 ? 2L * L : VV;
+            const long first = std::max(0L, r0 - base), last = std::min(count, r1 - base);
+            if (last <= first) continue;
+            const long nterms = last - first;
             // per-term scratch: all left environments, one site's X / Q / P, two R, G
             long envTot = 0, blk = 0, rmax = 0, gmax = 0;
             std::vector<long> eoff(L + 1);
@@ -501,8 +509,9 @@ struct Ops {
             double* val = sc.get<double>((size_t)Bw);
             double* g = sc.get<double>((size_t)Bw * NL * L);
             const AdjTerms<T> tm{op, coef, NL, L};
-            for (long t0 = 0; t0 < nterms; t0 += Bw) {
-                const int Bc = (int)std::min<long>(Bw, nterms - t0);
+            for (long j0 = 0; j0 < nterms; j0 += Bw) {
+                const int Bc = (int)std::min<long>(Bw, nterms - j0);
+                const long t0 = first + j0;
                 {
                     THC_LAUNCH("adj_terms", st());
                     k_adj_terms<T><<<Bc, 32, 0, st()>>>(kind, t0, Bc, L, N, H->t, H->chi, H->zeta, op, coef, weight);
