@@ -136,6 +136,19 @@ typedef struct {
 thc_status thc_apply_H(const thc_hamiltonian* H, const thc_mps* psi, const thc_opts* opts,
                        thc_mps* out, const thc_allocator* alloc, void* stream);
 
+/* Several independent H|psi> at once (e.g. instances of uneven L): out[i] =
+ * thc_apply_H(H[i], psi[i]) for i < n, with one opts for all.  Every instance
+ * runs on its own stream, forked from `stream` and joined back into it before
+ * the call returns (so `stream` orders after all of them), driven by its own
+ * host thread; their kernels run concurrently on the device.  With
+ * opts->batch = 0 the terms in flight are split between the instances
+ * (max(32, 4 * SMs / n) each).  H[i], psi[i]: as for thc_apply_H; all psi
+ * share one dtype.  out: caller array of n descriptors, each filled with a
+ * library-owned MPS.  On failure every output already made is released and the
+ * first failing instance's status is returned (its message names it). */
+thc_status thc_apply_H_batched(int n, const thc_hamiltonian* const* H, const thc_mps* const* psi,
+                               const thc_opts* opts, thc_mps* out, const thc_allocator* alloc, void* stream);
+
 /* One elementary MPO (a ladder operator sum_s coef_s a_{s,sigma}, or its
  * creation counterpart when dagger != 0) applied to psi and compressed
  * (Sec. 3.1, Fig. 3).  coef: device float64 [L]; sigma: 0 = up, 1 = down. */

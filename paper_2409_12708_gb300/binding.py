@@ -83,6 +83,8 @@ def _load():
                               P(thc_mps), P(C.c_double), P(thc_allocator), C.c_void_p],
         "thc_kinetic_factors": [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
         "mps_inner_noalloc": [P(thc_mps), P(thc_mps), P(C.c_double), C.c_void_p],
+        "thc_apply_H_batched": [C.c_int, P(P(thc_hamiltonian)), P(P(thc_mps)), P(thc_opts), P(thc_mps),
+                                P(thc_allocator), C.c_void_p],
         "thc_expect_grad": [P(thc_hamiltonian), P(thc_mps), P(thc_mps), P(thc_opts), P(C.c_double), C.c_void_p,
                             C.c_void_p, C.c_void_p, P(thc_mps), P(thc_allocator), C.c_void_p],
     }
@@ -108,7 +110,8 @@ LIB = _load()
 EXPORTED = ("thc_apply_H", "thc_layer_apply", "thc_compress", "mps_inner", "mps_add_compress",
             "krylov_lanczos_ground", "krylov_expm_apply", "thc_kinetic_factors", "thc_mps_free",
             "thc_last_error", "thc_build_info", "thc_kernel_launches", "thc_profile_enable",
-            "thc_profile_read", "mps_inner_noalloc", "krylov_lanczos_restarted", "thc_expect_grad")
+            "thc_profile_read", "mps_inner_noalloc", "krylov_lanczos_restarted", "thc_expect_grad",
+            "thc_apply_H_batched")
 
 
 # --------------------------------------------------------------------- allocator
@@ -220,6 +223,20 @@ def thc_apply_H(t, chi, zeta, psi, D_max, tol=0.0, path="fp64", term_begin=-1, t
         e.out_owner = out.owner  # what the failed call left in the output descriptor
         raise
     return _take(out)
+
+
+def thc_apply_H_batched(hams, psis, D_max, tol=0.0, path="fp64", batch=0):
+    """H_i|psi_i> for independent instances (hams: list of (t, chi, zeta)),
+    run concurrently on their own streams; returns the list of outputs."""
+    n = len(psis)
+    hs = [_ham(*h) for h in hams]
+    ds = [_desc(p) for p in psis]
+    harr = (C.POINTER(thc_hamiltonian) * n)(*[C.pointer(h) for h in hs])
+    parr = (C.POINTER(thc_mps) * n)(*[C.pointer(d) for d in ds])
+    outs = (thc_mps * n)()
+    o = _opts(D_max, tol, path, batch=batch)
+    _check(LIB.thc_apply_H_batched(n, harr, parr, C.byref(o), outs, C.byref(TORCH_ALLOCATOR), _stream()))
+    return [_take(outs[i]) for i in range(n)]
 
 
 def thc_layer_apply(psi, coef, sigma, dagger, D_max, tol=0.0, path="fp64"):

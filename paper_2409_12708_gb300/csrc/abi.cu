@@ -1,6 +1,7 @@
 // abi.cu -- extern "C" entry points declared in include/thc.h.
 #include <cmath>
 #include <string>
+#include <thread>
 #include <type_traits>
 
 #include "abi_impl.cuh"
@@ -130,6 +131,81 @@ thc_status thc_apply_H(const thc_hamiltonian* H, const thc_mps* psi, const thc_o
             using T = std::remove_pointer_t<decltype(tag)>;
             return apply_H_t<T>(H, psi, opts, out, alloc, stream);
         });
+    })
+}
+
+thc_status thc_apply_H_batched(int n, const thc_hamiltonian* const* H, const thc_mps* const* psi,
+                               const thc_opts* opts, thc_mps* out, const thc_allocator* alloc, void* stream) {
+    THC_GUARD({
+        if (n < 1 || !H || !psi || !out) throw Error(THC_EINVAL, "bad batched arguments");
+        check_opts(opts);
+        for (int i = 0; i < n; ++i) {
+            check_mps(psi[i], "psi");
+            check_ham(H[i], psi[i]->L);
+            check_path_dtype(psi[i], opts);
+            check_complex_dmax(psi[i]->dtype, opts);
+            if (psi[i]->dtype != psi[0]->dtype) throw Error(THC_EINVAL, "all instances share one dtype");
+        }
+        for (int i = 0; i < n; ++i) std::memset(&out[i], 0, sizeof(thc_mps));
+        // the instances' terms in flight share the device: split the default
+        thc_opts o = *opts;
+        if (o.batch <= 0) {
+            int dev = 0, sms = 152;
+            THC_CUDA(cudaGetDevice(&dev));
+            THC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            o.batch = std::max(32, 4 * sms / n);
+        }
+        const cudaStream_t parent = (cudaStream_t)stream;
+        int cur_dev = 0;
+        THC_CUDA(cudaGetDevice(&cur_dev));  // worker threads start on device 0: they take the caller's
+        cudaEvent_t fork;
+        THC_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+        THC_CUDA(cudaEventRecord(fork, parent));
+        std::vector<cudaStream_t> st(n, nullptr);
+        std::vector<cudaEvent_t> join(n, nullptr);
+        std::vector<thc_status> status(n, THC_OK);
+        std::vector<std::string> msg(n);
+        thc_status setup = THC_OK;
+        for (int i = 0; i < n && setup == THC_OK; ++i) {
+            if (cudaStreamCreateWithFlags(&st[i], cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming) != cudaSuccess ||
+                cudaStreamWaitEvent(st[i], fork, 0) != cudaSuccess)
+                setup = THC_ECUDA;
+        }
+        if (setup == THC_OK) {
+            // one host thread per instance: each drives its own engine on its own stream
+            std::vector<std::thread> th;
+            for (int i = 0; i < n; ++i)
+                th.emplace_back([&, i] {
+                    if (cudaSetDevice(cur_dev) != cudaSuccess) {
+                        status[i] = THC_ECUDA;
+                        msg[i] = "cudaSetDevice failed in the instance's thread";
+                        return;
+                    }
+                    status[i] = thc_apply_H(H[i], psi[i], &o, &out[i], alloc, (void*)st[i]);
+                    if (status[i] != THC_OK) msg[i] = thc_last_error();
+                });
+            for (auto& t : th) t.join();
+        }
+        for (int i = 0; i < n; ++i) {
+            if (st[i] && join[i]) {
+                cudaEventRecord(join[i], st[i]);
+                cudaStreamWaitEvent(parent, join[i], 0);
+            }
+        }
+        for (int i = 0; i < n; ++i) {
+            if (join[i]) cudaEventDestroy(join[i]);
+            if (st[i]) cudaStreamDestroy(st[i]);
+        }
+        cudaEventDestroy(fork);
+        if (setup != THC_OK) throw Error(THC_ECUDA, "could not create the instances' streams");
+        for (int i = 0; i < n; ++i)
+            if (status[i] != THC_OK) {
+                // release what the other instances returned; report the first failure
+                for (int j = 0; j < n; ++j) thc_mps_free(&out[j], alloc, stream);
+                return fail(status[i], "instance " + std::to_string(i) + ": " + msg[i]);
+            }
+        return THC_OK;
     })
 }
 

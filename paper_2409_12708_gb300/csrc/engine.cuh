@@ -17,7 +17,9 @@
 #include <mutex>
 #include <stdexcept>
 #include <string>
+#include <tuple>
 #include <type_traits>
+#include <typeinfo>
 #include <vector>
 
 #include "../../include/thc.h"

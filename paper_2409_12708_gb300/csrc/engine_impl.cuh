@@ -48,11 +48,8 @@ struct Engine {
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        static bool attrs_done = false;
-        if (!attrs_done) {
-            set_attrs();
-            attrs_done = true;
-        }
+        static std::once_flag attrs_once;  // engines may be built on several host threads
+        std::call_once(attrs_once, set_attrs);
     }
 
     // Opt in to large dynamic shared memory: the per-block limit minus the
@@ -83,30 +80,85 @@ struct Engine {
 
     bool tc = false;  // TF32 path: float32 contractions on the tensor cores (3xTF32)
 
-    // Batched GEMM of the compression: the tensor-core kernel on the TF32 path
-    // (float32 storage, output tiles at least 64 x 64), else the SIMT kernels.
+    // Batched GEMM of the compression.  On the TF32 path (float32 storage,
+    // output at least 64 x 64) a small autotuner picks the kernel: the first
+    // time a contraction of one kind (loader and store types) and shape, with a
+    // batch in one power-of-two bucket, runs in the process, the tensor-core
+    // and the SIMT kernel both run it and are timed with CUDA events; the
+    // faster is remembered for that key and run once more, so the output always
+    // comes from the kernel chosen.  Otherwise the SIMT kernels.
     template <class LA, class LB, class SC>
     void gemm(int batch, int M, int N, int K, const LA& la, const LB& lb, const SC& sc) {
         if constexpr (std::is_same<T, float>::value) {
             if (tc && batch > 0 && M >= 64 && N >= 64 && K >= 1) {
-                static bool attr = false;  // one opt-in per instantiation
-                if (!attr) {
+                static std::once_flag attr_once;  // one opt-in per instantiation
+                std::call_once(attr_once, [] {
                     THC_CUDA(cudaFuncSetAttribute(k_gemm_tc<LA, LB, SC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                   tc::SMEM));
-                    attr = true;
+                });
+                auto run_tc = [&] {
+                    dim3 grid(ceil_div(N, tc::BN), ceil_div(M, tc::BM), batch);
+                    k_gemm_tc<LA, LB, SC><<<grid, tc::THREADS, tc::SMEM, st>>>(M, N, K, la, lb, sc, dflag);
+                    THC_CUDA(cudaGetLastError());
+                    Profiler& p = profiler();
+                    if (p.on) {  // every contraction run on the tensor cores, tuning runs included
+                        std::lock_guard<std::mutex> g(p.mu);
+                        p.acc["tc_gemm_launches"].first += 1;
+                    }
+                };
+                auto run_simt = [&] { THC_CUDA(launch_gemm<T>(batch, M, N, K, la, lb, sc, st)); };
+                int bucket = 0;
+                while ((1 << bucket) < batch) ++bucket;
+                const GemmKey key{typeid(k_gemm_tc<LA, LB, SC>).hash_code(), M, N, K, bucket};
+                int pick = tuned(key);
+                if (pick < 0) {
+                    cudaEvent_t e[3];
+                    for (auto& x : e) THC_CUDA(cudaEventCreate(&x));
+                    THC_CUDA(cudaEventRecord(e[0], st));
+                    run_tc();
+                    THC_CUDA(cudaEventRecord(e[1], st));
+                    run_simt();
+                    THC_CUDA(cudaEventRecord(e[2], st));
+                    THC_CUDA(cudaEventSynchronize(e[2]));
+                    float t_tc = 0.f, t_simt = 0.f;
+                    THC_CUDA(cudaEventElapsedTime(&t_tc, e[0], e[1]));
+                    THC_CUDA(cudaEventElapsedTime(&t_simt, e[1], e[2]));
+                    for (auto& x : e) cudaEventDestroy(x);
+                    pick = t_tc <= t_simt ? 1 : 0;
+                    remember(key, pick);
                 }
-                dim3 grid(ceil_div(N, tc::BN), ceil_div(M, tc::BM), batch);
-                k_gemm_tc<LA, LB, SC><<<grid, tc::THREADS, tc::SMEM, st>>>(M, N, K, la, lb, sc, dflag);
-                THC_CUDA(cudaGetLastError());
-                Profiler& p = profiler();
-                if (p.on) {  // how many contractions ran on the tensor cores
-                    std::lock_guard<std::mutex> g(p.mu);
-                    p.acc["tc_gemm_launches"].first += 1;
-                }
+                if (pick == 1) run_tc();
+                else run_simt();
                 return;
             }
         }
         THC_CUDA(launch_gemm<T>(batch, M, N, K, la, lb, sc, st));
+    }
+
+    // the autotuner's table: kernel kind and shape -> 1 (tensor cores) or 0 (SIMT)
+    struct GemmKey {
+        size_t kind;
+        int M, N, K, bucket;
+        bool operator<(const GemmKey& o) const {
+            return std::tie(kind, M, N, K, bucket) < std::tie(o.kind, o.M, o.N, o.K, o.bucket);
+        }
+    };
+    static std::mutex& tune_mu() {
+        static std::mutex m;
+        return m;
+    }
+    static std::map<GemmKey, int>& tune_table() {
+        static std::map<GemmKey, int> t;
+        return t;
+    }
+    static int tuned(const GemmKey& k) {
+        std::lock_guard<std::mutex> g(tune_mu());
+        auto it = tune_table().find(k);
+        return it == tune_table().end() ? -1 : it->second;
+    }
+    static void remember(const GemmKey& k, int pick) {
+        std::lock_guard<std::mutex> g(tune_mu());
+        tune_table()[k] = pick;
     }
 
     // ---------------------------------------------------------------- work

@@ -372,7 +372,6 @@ struct Ops {
         }
         T* r = E.reduce(sc, buf, n, pf, D, std::max(1, std::min(n / 2, 4 * E.sms)));
         THC_CUDA(cudaMemcpyAsync(out, r, P.size * sizeof(T), cudaMemcpyDeviceToDevice, st()));
-        THC_CUDA(cudaStreamSynchronize(st()));
     }
 
     // ------------------------------------------------------------- Lanczos
@@ -441,18 +440,20 @@ struct Ops {
         }
         Ht.assign((size_t)nv * nv, tzero<Acc>());
         S.assign((size_t)nv * nv, tzero<Acc>());
-        Acc* col = sc.get<Acc>((size_t)nv);
-        std::vector<Acc> tmp(nv);
+        // columns k of Htil and S land in one device array (column-major), read back once
+        Acc* cols = sc.get<Acc>((size_t)2 * nv * nv);
         for (int k = 0; k < nv; ++k) {
-            inner_batched(nv, vbuf, sz, pf, wbuf + k * sz, 0, pf, col);
-            THC_CUDA(cudaMemcpyAsync(tmp.data(), col, nv * sizeof(Acc), cudaMemcpyDeviceToHost, st()));
-            THC_CUDA(cudaStreamSynchronize(st()));
-            for (int j = 0; j < nv; ++j) Ht[(size_t)j * nv + k] = tmp[j];
-            inner_batched(nv, vbuf, sz, pf, vbuf + k * sz, 0, pf, col);
-            THC_CUDA(cudaMemcpyAsync(tmp.data(), col, nv * sizeof(Acc), cudaMemcpyDeviceToHost, st()));
-            THC_CUDA(cudaStreamSynchronize(st()));
-            for (int j = 0; j < nv; ++j) S[(size_t)j * nv + k] = tmp[j];
+            inner_batched(nv, vbuf, sz, pf, wbuf + k * sz, 0, pf, cols + (size_t)k * nv);
+            inner_batched(nv, vbuf, sz, pf, vbuf + k * sz, 0, pf, cols + (size_t)(nv + k) * nv);
         }
+        std::vector<Acc> tmp((size_t)2 * nv * nv);
+        THC_CUDA(cudaMemcpyAsync(tmp.data(), cols, tmp.size() * sizeof(Acc), cudaMemcpyDeviceToHost, st()));
+        THC_CUDA(cudaStreamSynchronize(st()));
+        for (int k = 0; k < nv; ++k)
+            for (int j = 0; j < nv; ++j) {
+                Ht[(size_t)j * nv + k] = tmp[(size_t)k * nv + j];
+                S[(size_t)j * nv + k] = tmp[(size_t)(nv + k) * nv + j];
+            }
         return nv;
     }
 
