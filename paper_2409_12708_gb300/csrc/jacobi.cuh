@@ -183,6 +183,39 @@ __device__ __forceinline__ double fast_div(double a, double b) { return a / b; }
 __device__ __forceinline__ float fast_rsqrt(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double fast_rsqrt(double x) { return rsqrt(x); }
 
+// Warp sums of NV per-lane values (NV a power of two, at most 32), every lane
+// getting all NV totals: a reduce-scatter butterfly leaves value i's total on
+// the 32/NV lanes of group i (lane / (32/NV)), and one shuffle per value
+// broadcasts it from the group's first lane (NV - 1 + 5 - log2(NV) + NV
+// shuffles instead of 5 NV for NV independent butterflies).
+template <int NV, class RT>
+__device__ __forceinline__ void warp_sums_all(RT (&v)[NV]) {
+    static_assert(NV >= 1 && NV <= 32 && (NV & (NV - 1)) == 0, "power of two");
+    const int lane = threadIdx.x & 31;
+    RT w[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) w[i] = v[i];
+#pragma unroll
+    for (int lev = 0; (1 << lev) < NV; ++lev) {
+        const int o = 16 >> lev;
+        const int half = (NV >> lev) / 2;
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < NV / 2; ++i) {
+            if (i < half) {
+                const RT send = upper ? w[i] : w[half + i];
+                const RT keep = upper ? w[half + i] : w[i];
+                w[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
+        }
+    }
+    RT t = w[0];
+#pragma unroll
+    for (int o = 32 / NV / 2; o >= 1; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = __shfl_sync(0xffffffffu, t, i * (32 / NV));
+}
+
 // One step of K disjoint pair rotations on register-resident rows: every pair
 // (X[a], X[b]) of the map PM with both rows valid (bits of `vrows`) and both
 // norms above the floor is rotated so that the two rows become orthogonal.
@@ -206,7 +239,7 @@ __device__ __forceinline__ double fast_rsqrt(double x) { return rsqrt(x); }
 // and the rotation stays unitary.
 template <class T, int NPL, int NR, class PM>
 __device__ __forceinline__ int rotate_regs(T (&X)[NR][NPL], real_t<T> (&nrm)[NR], unsigned vrows, real_t<T> rt2,
-                                           real_t<T> floor2) {
+                                           real_t<T> floor2, unsigned& changed) {
     using RT = real_t<T>;
     constexpr bool CX = is_complex_v<T>;
     constexpr int K = PM::K;
@@ -305,6 +338,7 @@ __device__ __forceinline__ int rotate_regs(T (&X)[NR][NPL], real_t<T> (&nrm)[NR]
             }
             nrm[a] -= tgk;
             nrm[b] += tgk;
+            changed |= (1u << a) | (1u << b);
             ++nrot;
         }
     });
@@ -368,24 +402,23 @@ __device__ int jacobi_sweep_reg(const Rows<T>& rows, int p, int n, bool vec, rea
                 for (int e = 0; e < NPL; ++e) s2 += tabs2(X[i][e]);
                 nrm[i] = s2;
             }
-#pragma unroll
-            for (int o = 16; o >= 1; o >>= 1)
-#pragma unroll
-                for (int i = 0; i < 2 * R; ++i) nrm[i] += __shfl_xor_sync(0xffffffffu, nrm[i], o);
+            warp_sums_all<2 * R>(nrm);
+            unsigned changed = 0;
             if (rr == 0) {
                 static_for<0, 2 * R - 1>([&](auto sc) {
                     myrot += rotate_regs<T, NPL, 2 * R, CircleShift<R, decltype(sc)::value>>(X, nrm, vrows, rt2,
-                                                                                             floor2);
+                                                                                             floor2, changed);
                 });
             } else if ((vrows & lowR) && (vrows >> R)) {
                 static_for<0, R>([&](auto sc) {
                     myrot += rotate_regs<T, NPL, 2 * R, CrossShift<R, decltype(sc)::value>>(X, nrm, vrows, rt2,
-                                                                                            floor2);
+                                                                                            floor2, changed);
                 });
             }
+            // rows no rotation touched are unchanged in memory
 #pragma unroll
             for (int i = 0; i < 2 * R; ++i) {
-                if ((vrows >> i) & 1u) {
+                if ((vrows >> i) & (changed >> i) & 1u) {
                     const int blk = i < R ? A : Bk;
                     store_row<T, NPL>(X[i], rows(blk * R + (i < R ? i : i - R)), n, vec);
                 }

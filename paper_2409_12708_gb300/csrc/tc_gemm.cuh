@@ -20,7 +20,9 @@
 //     thread 4 rows' 4-element k-chunks of each), split them, and store them in
 //     the no-swizzle K-major canonical layout (8-row x 16-byte core matrices;
 //     k-chunks 128 bytes apart, 8-row groups 1 KB apart) with 16-byte stores
-//     that fill 512 contiguous bytes per warp; two stages;
+//     that fill 512 contiguous bytes per warp; two stages; the loads of
+//     slice k+1 are issued right after the MMAs of slice k, so their latency
+//     overlaps the tensor core's work and the read-back below;
 //   * one thread issues the 12 MMAs of a slice (K = 8 each) into the slice's
 //     accumulator pair and commits them to the stage's mbarrier;
 //   * while the tensor core works on slice k, the threads read back slice
@@ -152,14 +154,10 @@ k_gemm_tc(int M, int N, int K, LA la, LB lb, SC sc, int* status) {
     const int lr = lane & 7, lc = lane >> 3;
     uint32_t parity[2] = {0u, 0u};
     bool ok = true;
-    for (int kt = 0; kt < nkt && ok; ++kt) {
-        const int st = kt & 1;
-        unsigned char* a_hi = smem + st * STAGE;
-        unsigned char* a_lo = a_hi + PART;
-        unsigned char* b_hi = a_hi + 2 * PART;
-        unsigned char* b_lo = a_hi + 3 * PART;
+    // this thread's elements of slice kt: va/vb[j][e] = A(m0 + r, k) and B(k, n0 + r)
+    float va[4][4], vb[4][4];
+    auto load_slice = [&](int kt) {
         const int k0 = kt * BK;
-        float va[4][4], vb[4][4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int unit = warp * 4 + j;            // 0..31
@@ -172,6 +170,14 @@ k_gemm_tc(int M, int N, int K, LA la, LB lb, SC sc, int* status) {
                 vb[j][e] = (n0 + r < N && k < K) ? (float)lb(b, k, n0 + r) : 0.f;
             }
         }
+    };
+    if (nkt > 0) load_slice(0);
+    for (int kt = 0; kt < nkt && ok; ++kt) {
+        const int st = kt & 1;
+        unsigned char* a_hi = smem + st * STAGE;
+        unsigned char* a_lo = a_hi + PART;
+        unsigned char* b_hi = a_hi + 2 * PART;
+        unsigned char* b_lo = a_hi + 3 * PART;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int unit = warp * 4 + j;
@@ -214,6 +220,8 @@ k_gemm_tc(int M, int N, int K, LA la, LB lb, SC sc, int* status) {
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                 smem_u32(&mbar[st])));
         }
+        // the global loads of slice kt+1 are in flight during the wait below
+        if (kt + 1 < nkt) load_slice(kt + 1);
         // fold slice kt-1 into the registers while the tensor core runs slice kt
         // (the wait also frees stage kt-1's shared memory for slice kt+1)
         if (kt >= 1) {
