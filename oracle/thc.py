@@ -17,6 +17,18 @@ Term list (readings of the paper where it leaves the choice open):
   * The compressed terms are summed by the pairwise reduction of Fig. parallel:
     level by level, items 2j and 2j+1 are added and compressed, an odd last item
     moves up unchanged.
+  * Optional spin merge (merge_spin=True; the symmetric-zeta reading of Eq. thc):
+    for sig != sig' the one-body operators G_{mu sig} and G_{nu sig'} act on
+    different spin modes and commute, so with zeta = zeta^T the sum over
+    (mu down, nu up) equals the sum over (mu up, nu down) and the two merge
+    into zeta^{mu nu} G_{mu up} G_{nu down}.  Same-spin products do not commute
+    (the pair is [G_a, G_b] = (chi^a . chi^b)(A+_a A_b - A+_b A_a) apart) and
+    stay as they are.  Term list: 3 N^2 Coulomb terms, block by block,
+        t <  N^2        : block (nu = t // N, sig' = up),   mu = t % N, sig = up
+        t >= N^2, t' = t - N^2 :
+                          block (nu = t' // 2N, sig' = down), sig = (t' // N) % 2,
+                          mu = t' % N; the factor 2 on sig = up (the merged pair)
+    then the 2L kinetic terms.
 """
 from __future__ import annotations
 
@@ -31,8 +43,12 @@ def kinetic_factors(t: np.ndarray):
     return lam, u
 
 
-def n_terms(L: int, N: int) -> int:
-    return 4 * N * N + 2 * L
+def n_terms(L: int, N: int, merge_spin: bool = False) -> int:
+    return (3 if merge_spin else 4) * N * N + 2 * L
+
+
+def n_coulomb(N: int, merge_spin: bool = False) -> int:
+    return (3 if merge_spin else 4) * N * N
 
 
 def coulomb_index(mu, sig, nu, sigp, N):
@@ -50,6 +66,18 @@ def decode_term(tidx: int, L: int, N: int):
         sigp = rest // N
         return ("V", mu, sig, nu, sigp)
     k = tidx - 4 * N * N
+    return ("T", k % L, k // L)
+
+
+def decode_term_merged(tidx: int, L: int, N: int):
+    """('V', mu, sig, nu, sigp, factor) or ('T', i, sig) in the spin-merged list."""
+    if tidx < N * N:
+        return ("V", tidx % N, 0, tidx // N, 0, 1.0)
+    if tidx < 3 * N * N:
+        k = tidx - N * N
+        sig = (k // N) % 2
+        return ("V", k % N, sig, k // (2 * N), 1, 2.0 if sig == 0 else 1.0)
+    k = tidx - 3 * N * N
     return ("T", k % L, k // L)
 
 
@@ -80,23 +108,25 @@ def sequential_sum(items, D_max, tol):
     return phi
 
 
-def term_states(psi, t, chi, zeta, D_max, tol, term_begin=0, term_end=None):
+def term_states(psi, t, chi, zeta, D_max, tol, term_begin=0, term_end=None, merge_spin=False):
     """Compressed G|psi> / T|psi> for the terms in [term_begin, term_end), in order."""
     L, N = chi.shape
-    T = n_terms(L, N)
+    T = n_terms(L, N, merge_spin)
     term_end = T if term_end is None else term_end
     lam, u = kinetic_factors(t)
     reuse = {}
     out = []
     for tidx in range(term_begin, term_end):
-        kind = decode_term(tidx, L, N)
+        kind = decode_term_merged(tidx, L, N) if merge_spin else decode_term(tidx, L, N)
+        if kind[0] == "V" and not merge_spin:
+            kind = kind + (1.0,)
         if kind[0] == "V":
-            _, mu, sig, nu, sigp = kind
+            _, mu, sig, nu, sigp, factor = kind
             key = (nu, sigp)
             if key not in reuse:  # Alg. 1: psi_{nu sig'} from the two lower layers
                 x = apply_layer(psi, chi[:, nu], sigp, False, D_max, tol)
                 reuse[key] = apply_layer(x, chi[:, nu], sigp, True, D_max, tol)
-            x = M.scale(reuse[key], 0.5 * zeta[mu, nu])
+            x = M.scale(reuse[key], factor * 0.5 * zeta[mu, nu])
             x = apply_layer(x, chi[:, mu], sig, False, D_max, tol)
             x = apply_layer(x, chi[:, mu], sig, True, D_max, tol)
         else:
@@ -108,9 +138,9 @@ def term_states(psi, t, chi, zeta, D_max, tol, term_begin=0, term_end=None):
     return out
 
 
-def apply_H(psi, t, chi, zeta, D_max, tol=0.0, term_begin=0, term_end=None):
+def apply_H(psi, t, chi, zeta, D_max, tol=0.0, term_begin=0, term_end=None, merge_spin=False):
     """H|psi> as a compressed MPS: all terms, then the pairwise reduction."""
-    return pairwise_sum(term_states(psi, t, chi, zeta, D_max, tol, term_begin, term_end),
+    return pairwise_sum(term_states(psi, t, chi, zeta, D_max, tol, term_begin, term_end, merge_spin),
                         D_max, tol)
 
 
