@@ -60,6 +60,7 @@ def parse():
     p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (L=16, N=48, D=64) record")
     p.add_argument("--no-expm", action="store_true", help="skip the Krylov time-step record")
     p.add_argument("--no-config2", action="store_true", help="skip the L=24, N=96, D=256 slice record")
+    p.add_argument("--no-merge", action="store_true", help="skip the spin-merged H|psi> record")
     return p.parse_args()
 
 
@@ -421,6 +422,29 @@ def run_ours(args):
     stats = {k: prof.pop(k) for k in list(prof)
              if k.startswith("jacobi_sweeps") or k.startswith("jacobi_budget") or k == "tc_gemm_launches"}
 
+    # ---- the spin-merged term list (3N^2 Coulomb terms instead of 4N^2): one
+    # whole H|psi> on the same path, its time beside the timed step's, and its
+    # relative distance from the timed step's result (both truncated at D_max:
+    # the two term lists differ by their truncation errors)
+    merged = None
+    if not args.no_merge and args.terms == 0 and rank == 0:
+        Tm = 3 * w["N"] * w["N"] + 2 * w["L"]
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        om = B.thc_apply_H(*H, psi32, D_max=D, path=args.path, batch=args.batch, merge_spin=True)
+        e1.record()
+        e1.synchronize()
+        sm = e0.elapsed_time(e1) / 1e3
+        a = [x.double() for x in om]
+        b = [x.double() for x in out]
+        aa, bb, ab = B.mps_inner(a, a), B.mps_inner(b, b), B.mps_inner(a, b)
+        merged = {"terms": Tm, "hpsi_s": sm, "hpsi_per_s": 1.0 / sm, "speedup_vs_unmerged": ms_step / 1e3 / sm,
+                  "rel_distance_to_unmerged": float(np.sqrt(max(aa + bb - 2.0 * ab, 0.0) / bb)),
+                  "note": "opposite-spin Coulomb terms folded pairwise (G_{mu up}, G_{nu down} commute, zeta "
+                          "symmetric); same path and D_max as the timed step; distance by float64 inner "
+                          "products on the device"}
+
     # ---- float32 vs plain float64 on the same leading slice of terms, every term
     # of the slice in flight at once on both paths (so both fill the GPU alike);
     # the float32 result's distance from the float64 one is computed with float64
@@ -616,6 +640,7 @@ def run_ours(args):
         "adjoint": adjoint,
         "expm": expm,
         "config2": config2,
+        "merged_spin": merged,
     }
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(args)

@@ -115,7 +115,20 @@ typedef struct {
  * (0 = choose from free memory).  chunk: at most this many term states are
  * held before their partial sum is formed (rounded down to a power of two, so
  * every chunk is a whole subtree of the pairwise reduction and the result does
- * not depend on it; 0 = as many as a quarter of free memory holds). */
+ * not depend on it; 0 = as many as a quarter of free memory holds).
+ * merge_spin (0 = off, 1 = on; every call that applies H, including the Krylov
+ * calls; thc_expect_grad ignores it): fold the opposite-spin Coulomb terms
+ * pairwise.  For s != s' the one-body operators G_{mu s} and G_{nu s'} act on
+ * different spin modes and commute, so with zeta symmetric (Eq. thc) the terms
+ * (mu down, nu up) sum to the same operator as (mu up, nu down); the merged
+ * list keeps zeta^{mu nu} G_{mu up} G_{nu down} with twice the coefficient and
+ * drops the other, 3N^2 Coulomb terms instead of 4N^2 (same-spin products do
+ * not commute and stay).  Term indices then run block by block: t < N^2 is
+ * block (nu = t / N, s' = up) with mu = t % N, s = up; for t' = t - N^2 < 2N^2,
+ * block (nu = t' / 2N, s' = down), s = (t' / N) % 2, mu = t' % N; kinetic
+ * terms follow at 3N^2 + s*L + i.  Exact when zeta = zeta^T (the caller's
+ * responsibility); the truncated result differs from the unmerged one by
+ * truncation error, as any change of the term list does. */
 typedef struct {
     int D_max;
     double tol;
@@ -124,6 +137,7 @@ typedef struct {
     long term_end;
     int batch;
     int chunk;
+    int merge_spin;
 } thc_opts;
 
 /* H|psi> as a compressed MPS: Alg. 1 of the paper (the reuse of

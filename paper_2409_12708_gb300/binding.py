@@ -50,7 +50,7 @@ class thc_hamiltonian(C.Structure):
 class thc_opts(C.Structure):
     _fields_ = [("D_max", C.c_int), ("tol", C.c_double), ("path", C.c_int),
                 ("term_begin", C.c_long), ("term_end", C.c_long), ("batch", C.c_int),
-                ("chunk", C.c_int)]
+                ("chunk", C.c_int), ("merge_spin", C.c_int)]
 
 
 _ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -200,9 +200,9 @@ def _ham(t, chi, zeta):
     return h
 
 
-def _opts(D_max, tol, path, term_begin=-1, term_end=-1, batch=0, chunk=0):
+def _opts(D_max, tol, path, term_begin=-1, term_end=-1, batch=0, chunk=0, merge_spin=False):
     return thc_opts(int(D_max), float(tol), _PATHS[path], int(term_begin), int(term_end), int(batch),
-                    int(chunk))
+                    int(chunk), int(bool(merge_spin)))
 
 
 def _code(path):
@@ -211,10 +211,10 @@ def _code(path):
 
 # --------------------------------------------------------------------- entry points
 def thc_apply_H(t, chi, zeta, psi, D_max, tol=0.0, path="fp64", term_begin=-1, term_end=-1, batch=0,
-                chunk=0, allocator=None):
+                chunk=0, allocator=None, merge_spin=False):
     h = _ham(t, chi, zeta)
     d = _desc(psi, _code(path))
-    o = _opts(D_max, tol, path, term_begin, term_end, batch, chunk)
+    o = _opts(D_max, tol, path, term_begin, term_end, batch, chunk, merge_spin)
     out = thc_mps()
     al = allocator if allocator is not None else TORCH_ALLOCATOR
     try:
@@ -289,10 +289,11 @@ def mps_add_compress(coeffs, xs, D_max, tol=0.0, path="fp64"):
     return _take(out)
 
 
-def krylov_lanczos_ground(t, chi, zeta, psi0, K, D_max, tol=0.0, path="fp64", want_ground=False, batch=0):
+def krylov_lanczos_ground(t, chi, zeta, psi0, K, D_max, tol=0.0, path="fp64", want_ground=False, batch=0,
+                          merge_spin=False):
     h = _ham(t, chi, zeta)
     d = _desc(psi0, _code(path))
-    o = _opts(D_max, tol, path, batch=batch)
+    o = _opts(D_max, tol, path, batch=batch, merge_spin=merge_spin)
     e = C.c_double()
     ritz = (C.c_double * K)()
     g = thc_mps()

@@ -65,6 +65,7 @@ void check_opts(const thc_opts* o) {
     if (o->path != THC_PATH_FP64 && o->path != THC_PATH_FP32 && o->path != THC_PATH_TF32)
         throw Error(THC_EINVAL, "bad path");
     if (o->D_max > 512) throw Error(THC_EUNSUPPORTED, "D_max above 512 is not supported");
+    if (o->merge_spin != 0 && o->merge_spin != 1) throw Error(THC_EINVAL, "merge_spin must be 0 or 1");
 }
 
 void check_ham(const thc_hamiltonian* H, int L) {

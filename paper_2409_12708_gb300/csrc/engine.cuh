@@ -475,8 +475,49 @@ __global__ void k_copy_batched(T* dst, long sdst, const T* src, long ssrc, long 
 //      source = reuse slot (s'*N + nu) - j_first;
 //    kinetic t -> (i, s): layer 1 = lambda_i sum_q u_qi a_{q s}, layer 2 = sum_p u_pi a+_{p s},
 //      source = 0 (psi itself).
+// Coulomb term list (Eq. G).  Unmerged: t = ((s'*N + nu)*2 + s)*N + mu, 4N^2
+// terms.  Spin-merged (symmetric zeta): the opposite-spin pair (mu down, nu up)
+// is folded into (mu up, nu down), which commute and carry the same zeta; the
+// list is block (nu, up) with mu up only (t < N^2), then block (nu, down)
+// with s = up (factor 2) and s = down, 3N^2 terms.  block = s'*N + nu is the
+// index of the reused state psi_{nu s'}.
+struct TermIdx {
+    int mu, s, nu, sp;
+    double factor;
+};
+__host__ __device__ inline long coulomb_terms(int N, int merge) { return (merge ? 3L : 4L) * N * N; }
+__host__ __device__ inline TermIdx decode_coulomb(long t, int N, int merge) {
+    TermIdx d;
+    d.factor = 1.0;
+    if (!merge) {
+        d.mu = (int)(t % N);
+        long rest = t / N;
+        d.s = (int)(rest % 2);
+        rest /= 2;
+        d.nu = (int)(rest % N);
+        d.sp = (int)(rest / N);
+    } else if (t < (long)N * N) {
+        d.mu = (int)(t % N);
+        d.s = 0;
+        d.nu = (int)(t / N);
+        d.sp = 0;
+    } else {
+        const long k = t - (long)N * N;
+        d.mu = (int)(k % N);
+        d.s = (int)((k / N) % 2);
+        d.nu = (int)(k / (2L * N));
+        d.sp = 1;
+        if (d.s == 0) d.factor = 2.0;
+    }
+    return d;
+}
+__host__ __device__ inline long coulomb_block(long t, int N, int merge) {
+    const TermIdx d = decode_coulomb(t, N, merge);
+    return (long)d.sp * N + d.nu;
+}
+
 template <class T>
-__global__ void k_term_coefs(int stage, long t0, int B, int L, int N, const double* chi,
+__global__ void k_term_coefs(int stage, long t0, int B, int L, int N, int merge, const double* chi,
                              const double* zeta, const double* lam, const double* u,
                              long j_first, T* coef1, T* coef2, int* op1, int* op2, int* src) {
     const int b = blockIdx.x;
@@ -491,19 +532,14 @@ __global__ void k_term_coefs(int stage, long t0, int B, int L, int N, const doub
         col = nu;
         sig = sp;
         source = 0;
-    } else if (t < 4L * N * N) {
-        const int mu = (int)(t % N);
-        long rest = t / N;
-        const int s = (int)(rest % 2);
-        rest /= 2;
-        const int nu = (int)(rest % N);
-        const int sp = (int)(rest / N);
-        col = mu;
-        sig = s;
-        scale = 0.5 * zeta[(long)mu * N + nu];
-        source = (int)((long)sp * N + nu - j_first);
+    } else if (t < coulomb_terms(N, merge)) {
+        const TermIdx d = decode_coulomb(t, N, merge);
+        col = d.mu;
+        sig = d.s;
+        scale = d.factor * 0.5 * zeta[(long)d.mu * N + d.nu];
+        source = (int)((long)d.sp * N + d.nu - j_first);
     } else {
-        const long kk = t - 4L * N * N;
+        const long kk = t - coulomb_terms(N, merge);
         const int i = (int)(kk % L), s = (int)(kk / L);
         kinetic = true;
         col = i;

@@ -242,7 +242,9 @@ struct Ops {
             k_kinetic_factors<<<1, 256, KINETIC_SMEM, st()>>>(L, H->t, lam, u, E.dflag);
         }
         E.check();
-        const long TT = 4L * N * N + 2L * L;
+        const int merge = o->merge_spin ? 1 : 0;
+        const long VV = coulomb_terms(N, merge);
+        const long TT = VV + 2L * L;
         const long t0 = std::max(0L, o->term_begin < 0 ? 0L : o->term_begin);
         const long t1 = (o->term_end < 0) ? TT : std::min(TT, o->term_end);
         const long nT = t1 - t0;
@@ -254,11 +256,12 @@ struct Ops {
         Plan PD = make_plan<T>(MODE_DIRSUM, pf, pf, D);
         if (PA2.out != pf || PB2.out != pf || PD.out != pf)
             throw Error(THC_EINVAL, "input bonds below the full profile of D_max");
-        const long VV = 4L * N * N;
         const long cEnd = std::min(t1, VV);
         const bool hasV = t0 < cEnd;
-        const long j_first = hasV ? t0 / (2L * N) : 0;
-        const long nslots = hasV ? (cEnd - 1) / (2L * N) - j_first + 1 : 0;
+        // the reused states psi_{nu s'} the range needs: blocks are contiguous in
+        // the term order (both lists), so they are the slots j_first .. j_last
+        const long j_first = hasV ? coulomb_block(t0, N, merge) : 0;
+        const long nslots = hasV ? coulomb_block(cEnd - 1, N, merge) - j_first + 1 : 0;
         // batch (terms in flight)
         const std::vector<const Plan*> plans{&PA1, &PA2, &PB1, &PB2, &PD};
         const size_t per_term = Engine<T>::work_bytes_per_term(plans) +
@@ -278,7 +281,7 @@ struct Ops {
             const int Bc = (int)std::min<long>(Bw, nslots - j0);
             {
                 THC_LAUNCH("term_coefs", st());
-                k_term_coefs<T><<<Bc, 64, 0, st()>>>(0, j_first + j0, Bc, L, N, H->chi, H->zeta, lam, u,
+                k_term_coefs<T><<<Bc, 64, 0, st()>>>(0, j_first + j0, Bc, L, N, merge, H->chi, H->zeta, lam, u,
                                                       j_first, w.coef1, w.coef2, w.op1, w.op2, w.src);
             }
             E.check();
@@ -320,7 +323,7 @@ struct Ops {
                 const int Bc = (int)(w1 - w0);
                 {
                     THC_LAUNCH("term_coefs", st());
-                    k_term_coefs<T><<<Bc, 64, 0, st()>>>(1, t, Bc, L, N, H->chi, H->zeta, lam, u, j_first,
+                    k_term_coefs<T><<<Bc, 64, 0, st()>>>(1, t, Bc, L, N, merge, H->chi, H->zeta, lam, u, j_first,
                                                           w.coef1, w.coef2, w.op1, w.op2, w.src);
                 }
                 E.check();
