@@ -61,6 +61,7 @@ def parse():
     p.add_argument("--no-expm", action="store_true", help="skip the Krylov time-step record")
     p.add_argument("--no-config2", action="store_true", help="skip the L=24, N=96, D=256 slice record")
     p.add_argument("--no-merge", action="store_true", help="skip the spin-merged H|psi> record")
+    p.add_argument("--no-peaks", action="store_true", help="skip the cuBLAS GEMM rate measurement")
     return p.parse_args()
 
 
@@ -208,7 +209,39 @@ def fp32_alu_peak_tflops(sm_mhz, sms):
     return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
-def roofline(prof, stats, models, clocks, sms, peaks=None):
+def measure_gemm_peaks(torch):
+    """Dense GEMM rates of this GPU through cuBLAS (torch.matmul), the
+    denominators the measured-peaks file lacks: TF32 tensor (8192^3, float32
+    inputs with TF32 allowed), FP32 SIMT (same shape, TF32 off) and FP64
+    (4096^3).  Best of 5 after 2 warm-up calls, CUDA events; a second of GPU
+    time in all."""
+    def rate(n, dtype, tf32, reps=5):
+        old = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        try:
+            a = torch.randn(n, n, device="cuda", dtype=dtype)
+            b = torch.randn(n, n, device="cuda", dtype=dtype)
+            for _ in range(2):
+                a @ b
+            best = None
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                a @ b
+                e1.record()
+                e1.synchronize()
+                ms = e0.elapsed_time(e1)
+                best = ms if best is None else min(best, ms)
+            return 2.0 * n ** 3 / (best / 1e3) / 1e12
+        finally:
+            torch.backends.cuda.matmul.allow_tf32 = old
+    return {"tf32_tflops": rate(8192, torch.float32, True), "fp32_simt_tflops": rate(8192, torch.float32, False),
+            "fp64_tflops": rate(4096, torch.float64, False),
+            "note": "cuBLAS via torch.matmul on this GPU: TF32 8192^3, FP32 8192^3 (TF32 off), FP64 4096^3; "
+                    "best of 5 after 2 warm-up calls"}
+
+
+def roofline(prof, stats, models, clocks, sms, peaks=None, tf32_measured=None):
     """Roofline object of the dominant unit class of a profiled step.
 
     prof: {profile name: {"launches", "ms"}} from the library's CUDA-event
@@ -233,7 +266,12 @@ def roofline(prof, stats, models, clocks, sms, peaks=None):
     unit, rec = max(by_unit.items(), key=lambda kv: kv[1]["ms"])
     sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
     peak = fp32_alu_peak_tflops(sm_mhz, sms)
-    tf32 = 0.5 * peaks["bf16_tflops_sustained"] if peaks and "bf16_tflops_sustained" in peaks else None
+    if tf32_measured:
+        tf32, tf32_src = tf32_measured, "the measured cuBLAS TF32 GEMM rate of this run"
+    elif peaks and "bf16_tflops_sustained" in peaks:
+        tf32, tf32_src = 0.5 * peaks["bf16_tflops_sustained"], "1/2 of the measured BF16 sustained rate"
+    else:
+        tf32, tf32_src = None, "not available"
     summary = {}
     for u, r in by_unit.items():
         a = models.get(u, 0.0) / (r["ms"] / 1e3) / 1e12
@@ -258,8 +296,7 @@ def roofline(prof, stats, models, clocks, sms, peaks=None):
             "traffic": traffic, "traffic_unit": "DRAM bytes per launch (ncu, scaled by matrices per launch)",
             "launches_per_step": rec["launches"], "ms_per_step": rec["ms"], "by_unit": summary,
             "peak_note": f"FP32 SIMT peak derived from the device: {sms} SMs x 128 lanes x 2 flop x "
-                         f"{sm_mhz:.0f} MHz (median SM clock under load); TF32 tensor peak = 1/2 of the "
-                         "measured BF16 sustained rate (MEASURED_PEAKS.json)"}
+                         f"{sm_mhz:.0f} MHz (median SM clock under load); TF32 tensor peak = {tf32_src}"}
 
 
 def read_golden(path):
@@ -617,7 +654,9 @@ def run_ours(args):
     peaks = None
     if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")):
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    roof = roofline(prof, stats, models, clocks, sms, peaks)
+    gemm_peaks = None if args.no_peaks else measure_gemm_peaks(torch)
+    roof = roofline(prof, stats, models, clocks, sms, peaks,
+                    tf32_measured=gemm_peaks["tf32_tflops"] if gemm_peaks else None)
     line = {
         "metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -635,12 +674,15 @@ def run_ours(args):
         "kernel_ms_per_step": {k: round(v["ms"], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])},
         "jacobi_sweeps_per_svd": {k: round(v["ms"] / max(v["launches"], 1), 2) for k, v in stats.items()
                                   if k.startswith("jacobi_sweeps")},
+        "jacobi_budget_exhausted": int(stats["jacobi_budget_exhausted"]["launches"])
+        if "jacobi_budget_exhausted" in stats else 0,
         "compressions_per_step": n_compress,
         "krylov": krylov,
         "adjoint": adjoint,
         "expm": expm,
         "config2": config2,
         "merged_spin": merged,
+        "gemm_peaks": gemm_peaks,
     }
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(args)

@@ -48,9 +48,11 @@ typedef enum {
     THC_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed             */
     THC_ENONFINITE = 4,    /* a NaN/Inf was detected in an input or a result          */
     THC_ETIMEOUT = 5,      /* the small float64 eigensolver ran out of sweeps (a Jacobi
-                              SVD that ends its sweep budget is not an error: its
-                              result stays exact through the projector correction;
-                              it is counted in the profile)                           */
+                              SVD that ends its sweep budget is counted in the
+                              profile, not raised: untruncated, the projector
+                              correction keeps the state exact; truncating, the
+                              kept rows are orthogonal only to the last sweep's
+                              largest rotation, so the result can be off)           */
     THC_EBREAKDOWN = 6,    /* Krylov breakdown: the Krylov space is exhausted         */
     THC_EUNSUPPORTED = 7   /* valid request this build does not implement             */
 } thc_status;

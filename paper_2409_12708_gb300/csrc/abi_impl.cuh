@@ -69,9 +69,9 @@ struct Call {
             return THC_ETIMEOUT;
         }
         if (f & thc::DEV_NONCONVERGED) {
-            // not an error: the projector correction keeps the state exact and the
-            // kept subspace is orthogonal to the rotation threshold of the last
-            // sweep; counted, with the rotations that sweep still applied
+            // counted, with the rotations the last sweep still applied: untruncated
+            // the projector correction keeps the state exact; truncating, the kept
+            // rows are orthogonal only to that sweep's largest rotation
             auto& p = thc::profiler();
             std::lock_guard<std::mutex> g(p.mu);
             auto& x = p.acc["jacobi_budget_exhausted"];

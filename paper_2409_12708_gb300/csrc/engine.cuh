@@ -260,7 +260,7 @@ inline Plan make_plan(int mode, const std::vector<int>& inA, const std::vector<i
         P.maxKout = std::max<long>(P.maxKout, P.out[s + 1]);
         P.maxP = std::max(P.maxP, p);
         P.maxN = std::max(P.maxN, n);
-        if (m > n) {
+        if (m >= n) {
             int nb;
             qr_params<T>(m, n, nb);
             P.maxTw = std::max(P.maxTw, (long)ceil_div(n, nb) * nb * nb);

@@ -286,7 +286,7 @@ struct Engine {
         for (int s = 0; s < L - 1; ++s) {
             const int m = 4 * P.out[s], n = P.k[s + 1], kout = P.out[s + 1];
             // C_s = M_{s-1} Q_s  (M_{-1} = [1], Q_0 = X_0)
-            StoreC<T> sto{w.C, w.sC, m > n ? w.W : nullptr, w.sC, m, n, 4 * n};
+            StoreC<T> sto{w.C, w.sC, m >= n ? w.W : nullptr, w.sC, m, n, 4 * n};
             RowMajorB<T> qop{w.wide + P.woff[s], w.sWide, 4 * n};
             if (s == 0) {
                 THC_LAUNCH("gemm_center", st);
@@ -298,8 +298,10 @@ struct Engine {
             }
             int p = std::min(m, n);
             const int* colmap = nullptr;
-            if (m > n) {
-                // block-pivoted QR: the kernel writes the column order it chose to w.perm
+            if (m >= n) {
+                // block-pivoted QR (square factors too: an unpivoted square C with a
+                // numerically null part can take the Jacobi past its sweep budget):
+                // the kernel writes the column order it chose to w.perm
                 colmap = w.perm;
                 QRJob<T> job;
                 job.colmap = w.perm;

@@ -1,8 +1,9 @@
 // jacobi.cuh -- truncated SVD of one compression step (Fig. 3, SVD sweep).
 //
 // Input per term: Z (p x n, row-major) with Z^H Z = C^H C, where C is the site
-// matrix [(chi_l, n_phys) x k] being truncated (Z = R from a Householder QR of
-// C when C is tall, Z = C otherwise).  One-sided Jacobi (Hestenes) rotates
+// matrix [(chi_l, n_phys) x k] being truncated (Z = R from a block-pivoted
+// Householder QR of C when C has at least as many rows as columns, Z = C
+// otherwise).  One-sided Jacobi (Hestenes) rotates
 // pairs of rows of Z until all rows are mutually orthogonal; rotations are
 // unitary, so Z^H Z = C^H C is preserved and the rows end up as
 // sigma_j v_j^H with v_j the right singular vectors of C (v_j^T for real C).  Rows are visited in

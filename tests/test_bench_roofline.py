@@ -45,6 +45,11 @@ def test_dominant_unit_groups_precond_qr_with_jacobi():
     assert r["peak_tensor_tf32"] == 850.0
     qr = r["by_unit"]["qr"]
     assert abs(qr["achieved_tflops"] - 3.0e16 / 6.0631 / 1e12) < 1e-9
+    # a TF32 rate measured in the run replaces the BF16-derived estimate
+    r2 = bench.roofline(prof, stats, models, {"sm_mhz": 2070.0}, sms=148,
+                        peaks={"bf16_tflops_sustained": 1700.0}, tf32_measured=1000.0)
+    assert r2["peak_tensor_tf32"] == 1000.0 and r2["frac_tensor_tf32"] == r2["achieved"] / 1000.0
+    assert "measured cuBLAS TF32" in r2["peak_note"]
 
 
 def test_traffic_scaled_by_matrices_and_tied_to_source(tmp_path, monkeypatch):
