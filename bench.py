@@ -62,6 +62,7 @@ def parse():
     p.add_argument("--no-config2", action="store_true", help="skip the L=24, N=96, D=256 slice record")
     p.add_argument("--no-merge", action="store_true", help="skip the spin-merged H|psi> record")
     p.add_argument("--no-peaks", action="store_true", help="skip the cuBLAS GEMM rate measurement")
+    p.add_argument("--no-batched", action="store_true", help="skip the batched-instances record")
     return p.parse_args()
 
 
@@ -482,6 +483,38 @@ def run_ours(args):
                           "symmetric); same path and D_max as the timed step; distance by float64 inner "
                           "products on the device"}
 
+    # ---- independent instances of uneven L in one call (thc_apply_H_batched):
+    # 8 Hamiltonians L = 8..16, N = 2L, half-filled states at D_max = 32, on
+    # the same path; the batched call against the 8 single calls in sequence
+    batched = None
+    if not args.no_batched and rank == 0:
+        Ls = (8, 10, 12, 14, 16, 16, 12, 10)
+        hams, psis = [], []
+        for k, Lb in enumerate(Ls):
+            tb, cb, zb = thc_hamiltonian(Lb, 2 * Lb, seed=100 + k)
+            hams.append((dev(tb), dev(cb), dev(zb)))
+            psis.append([dev(a, torch.float32) for a in sector_mps(Lb, Lb // 2, Lb // 2, 32, seed=200 + k)])
+        Tb = sum(4 * (2 * Lb) ** 2 + 2 * Lb for Lb in Ls)
+        B.thc_apply_H_batched(hams[:2], psis[:2], D_max=32, path=args.path)  # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for h, pp in zip(hams, psis):
+            B.thc_apply_H(*h, pp, D_max=32, path=args.path)
+        e1.record()
+        e1.synchronize()
+        s_seq = e0.elapsed_time(e1) / 1e3
+        e0.record()
+        B.thc_apply_H_batched(hams, psis, D_max=32, path=args.path)
+        e1.record()
+        e1.synchronize()
+        s_bat = e0.elapsed_time(e1) / 1e3
+        batched = {"instances": [f"L{Lb}_N{2 * Lb}_D32" for Lb in Ls], "terms": Tb, "path": args.path,
+                   "sequential_s": s_seq, "batched_s": s_bat, "batched_terms_per_s": Tb / s_bat,
+                   "speedup": s_seq / s_bat,
+                   "note": "8 independent H|psi> (own Hamiltonian and state each) in one call, one stream per "
+                           "instance, against the 8 single calls in sequence on one stream"}
+
     # ---- float32 vs plain float64 on the same leading slice of terms, every term
     # of the slice in flight at once on both paths (so both fill the GPU alike);
     # the float32 result's distance from the float64 one is computed with float64
@@ -683,6 +716,7 @@ def run_ours(args):
         "config2": config2,
         "merged_spin": merged,
         "gemm_peaks": gemm_peaks,
+        "batched_instances": batched,
     }
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(args)
