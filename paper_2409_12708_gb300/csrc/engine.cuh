@@ -28,6 +28,7 @@
 #include "scalar.cuh"
 #include "jacobi.cuh"
 #include "qr.cuh"
+#include "qt_apply.cuh"
 #include "small.cuh"
 #include "tc_gemm.cuh"
 

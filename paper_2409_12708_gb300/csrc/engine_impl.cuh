@@ -18,6 +18,7 @@ template <class T>
 struct Work {
     int B = 0;
     long sWide = 0, sL = 0, sC = 0, sZ = 0, sV = 0, sTw = 0, sSv = 0;
+    long sTwSite = 0;  // T matrices of one site's QR; sTw = sites x sTwSite per term
     T *wide = nullptr, *Lb[2] = {nullptr, nullptr}, *C = nullptr, *W = nullptr, *Z = nullptr;
     T *V = nullptr, *M[2] = {nullptr, nullptr}, *Tw = nullptr;
     double* sv = nullptr;
@@ -74,6 +75,7 @@ struct Engine {
         opt_in(k_kinetic_factors, (int)KINETIC_SMEM);
         opt_in(k_krylov_small, (int)KRYLOV_SMEM);
         opt_in(k_krylov_small_c, (int)KRYLOV_SMEM_C);
+        if constexpr (std::is_same<T, float>::value) opt_in(k_apply_qt, big);
     }
 
     void check() { THC_CUDA(cudaGetLastError()); }
@@ -181,7 +183,10 @@ struct Engine {
         w.sC = up(mx.maxC);
         w.sZ = up(mx.maxZ);
         w.sV = up(mx.maxV);
-        w.sTw = up(mx.maxTw);
+        // every site keeps its QR's T matrices until the SVD sweep applies its Q
+        const long sites = plans.empty() ? 1 : std::max(1, plans[0]->L);
+        w.sTwSite = up(mx.maxTw);
+        w.sTw = sites * w.sTwSite;
         w.sSv = up(mx.maxKout);
         w.wide = sc.get<T>((size_t)B * w.sWide);
         w.Lb[0] = sc.get<T>((size_t)B * w.sL);
@@ -226,7 +231,7 @@ struct Engine {
             kout = std::max(kout, p->maxKout);
             L = p->L;
         }
-        return sizeof(T) * (size_t)(wsize + 2 * maxL + 2 * maxC + maxZ + 3 * maxV + maxTw + 2 * L + 2) +
+        return sizeof(T) * (size_t)(wsize + 2 * maxL + 2 * maxC + maxZ + 3 * maxV + (long)L * maxTw + 2 * L + 2) +
                sizeof(double) * kout + 8 * sizeof(int);
     }
 
@@ -240,6 +245,9 @@ struct Engine {
         Profile pA(P.inA), pO(P.out);
         Profile pB = P.mode == MODE_DIRSUM ? Profile(P.inB) : Profile();
         ex.L = L;
+        // sites whose Q is applied to M_{s-1} in the SVD sweep instead of being
+        // formed (real float32, 32-column panels, m <= 1024)
+        std::vector<char> qt(L + 1, 0);
         // ---- QR sweep, right to left: X_s = expand(site s) * L_{s+1}; X_s = L_s Q_s
         for (int s = L - 1; s >= 0; --s) {
             ex.s = s;
@@ -267,12 +275,14 @@ struct Engine {
                 job.m = 4 * P.k[s + 1];
                 job.n = P.e[s];
                 job.ld = job.m;
-                job.Tw = w.Tw;
+                job.Tw = w.Tw + (long)s * w.sTwSite;
                 job.strideT = w.sTw;
                 job.out = w.Lb[s & 1];
                 job.strideOut = w.sL;
                 qr_params<T>(job.m, job.n, job.nb);
-                job.mode = QR_L_AND_Q;
+                if constexpr (std::is_same<T, float>::value)
+                    qt[s] = job.nb == QT_NB && job.m <= 1024 && (int)qt_smem_bytes(job.m) <= smem_optin - 2048;
+                job.mode = qt[s] ? QR_L_ONLY : QR_L_AND_Q;
                 job.colmap = nullptr;
                 job.pivot = 0;
                 {
@@ -291,6 +301,9 @@ struct Engine {
             if (s == 0) {
                 THC_LAUNCH("gemm_center", st);
                 gemm(B, P.out[0], 4 * n, 1, IdentA<T>{}, qop, sto);
+            } else if (qt[s]) {
+                THC_LAUNCH("qt_apply", st);
+                apply_qt(B, P, s, w, w.C, w.sC, 4 * n, m >= n ? w.W : nullptr, n);
             } else {
                 RowMajorA<T> mop{w.M[(s - 1) & 1], w.sV, P.k[s]};
                 THC_LAUNCH("gemm_center", st);
@@ -358,11 +371,47 @@ struct Engine {
         // ---- last site: M_{L-2} Q_{L-1}
         {
             const int s = L - 1;
-            RowMajorA<T> mop{w.M[(s - 1) & 1], w.sV, P.k[s]};
-            RowMajorB<T> qop{w.wide + P.woff[s], w.sWide, 4 * P.k[s + 1]};
-            StoreRM<T> so{out + pO.off[s], out_stride, 4 * P.k[s + 1]};
-            THC_LAUNCH("gemm_center", st);
-            gemm(B, P.out[s], 4 * P.k[s + 1], P.k[s], mop, qop, so);
+            if (qt[s]) {
+                THC_LAUNCH("qt_apply", st);
+                apply_qt(B, P, s, w, out + pO.off[s], out_stride, 4 * P.k[s + 1], nullptr, 1);
+            } else {
+                RowMajorA<T> mop{w.M[(s - 1) & 1], w.sV, P.k[s]};
+                RowMajorB<T> qop{w.wide + P.woff[s], w.sWide, 4 * P.k[s + 1]};
+                StoreRM<T> so{out + pO.off[s], out_stride, 4 * P.k[s + 1]};
+                THC_LAUNCH("gemm_center", st);
+                gemm(B, P.out[s], 4 * P.k[s + 1], P.k[s], mop, qop, so);
+            }
+        }
+    }
+
+    // C = M_{s-1} Q_s from the reflectors the QR sweep left at site s (real
+    // float32 only; qt_apply.cuh)
+    void apply_qt(int B, const Plan& P, int s, Work<T>& w, T* C, long strideC, int ldC, T* W, int nW) {
+        if constexpr (std::is_same<T, float>::value) {
+            QtJob<float> j;
+            j.M = w.M[(s - 1) & 1];
+            j.strideM = w.sV;
+            j.ldM = P.k[s];
+            j.A = w.wide + P.woff[s];
+            j.strideA = w.sWide;
+            j.ld = 4 * P.k[s + 1];
+            j.Tw = w.Tw + (long)s * w.sTwSite;
+            j.strideT = w.sTw;
+            j.out = P.out[s];
+            j.m = 4 * P.k[s + 1];
+            j.kk = P.k[s];
+            j.C = C;
+            j.strideC = strideC;
+            j.ldC = ldC;
+            j.W = W;
+            j.strideW = w.sC;
+            j.nW = nW;
+            dim3 g(ceil_div(j.out, QT_RB), B);
+            k_apply_qt<<<g, QT_THREADS, qt_smem_bytes(j.m), st>>>(j);
+            check();
+        } else {
+            (void)B; (void)P; (void)s; (void)w; (void)C; (void)strideC; (void)ldC; (void)W; (void)nW;
+            throw Error(THC_EINVAL, "reflector application is float32 only");
         }
     }
 

@@ -18,6 +18,8 @@
 //                A holds X^T, so X = L Q^T and Q^T becomes the site tensor; for
 //                complex X the plain transpose keeps Q^T's rows orthonormal).
 //   QR_R_ROWS  : writes R (n x n, row-major, zero below the diagonal); m >= n.
+//   QR_L_ONLY  : writes L as QR_L_AND_Q and leaves the reflectors in A and the
+//                panel T matrices in Tw (Q is applied later without being formed).
 #pragma once
 
 #include "common.cuh"
@@ -25,7 +27,7 @@
 
 namespace thc {
 
-enum QRMode : int { QR_L_AND_Q = 1, QR_R_ROWS = 2 };
+enum QRMode : int { QR_L_AND_Q = 1, QR_R_ROWS = 2, QR_L_ONLY = 3 };
 
 template <class T>
 struct QRJob {
@@ -706,11 +708,12 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr(QRJob<T> job) {
             for (int c = tid; c < n; c += nt) job.colmap[(long)b * n + c] = pm[c];
         return;
     }
-    // QR_L_AND_Q: L = R^T (n x kk)
+    // QR_L_AND_Q / QR_L_ONLY: L = R^T (n x kk)
     for (int i = tid; i < n * kk; i += nt) {
         const int r = i / kk, c = i % kk;
         out[i] = (c <= r) ? A[(long)QCOL(r) * ld + c] : tzero<T>();
     }
+    if (job.mode == QR_L_ONLY) return;
     __syncthreads();
     // form Q in place, panels in reverse order
     const int npan = ceil_div(kk, nb);
