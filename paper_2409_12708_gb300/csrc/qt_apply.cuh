@@ -19,8 +19,9 @@
 //     (global; the zero/one substitution of V's triangle only on the panel's
 //     first 32 rows); the 16 warp partials are summed in shared memory;
 //   * Z <- Z T_p^T (T upper triangular);
-//   * X[:, p0:] -= Z V_p^T: one column of X per thread, V's row k read with
-//     coalesced loads across the warp.
+//   * X[:, p0:] -= Z V_p^T: two adjacent columns of X per thread, V's rows
+//     k, k+1 read with one 8-byte load per panel column, coalesced across the
+//     warp.
 // Real float32 only, panels of 32 columns, m <= 1024 (the LQ-sweep shapes of
 // the float paths up to D_max = 256); other shapes form Q in the QR kernel.
 #pragma once
@@ -154,30 +155,42 @@ static __global__ void __launch_bounds__(QT_THREADS, 1) k_apply_qt(QtJob<float> 
             Z2[o] = s;
         }
         __syncthreads();
-        // ---- X[:, p0:m] -= Z2 V_p^T, one column per thread
-        for (int k = p0 + tid; k < m; k += QT_THREADS) {
-            float v[QT_NB];
+        // ---- X[:, p0:m] -= Z2 V_p^T, two adjacent columns per thread (p0 and m
+        // are even): V's rows k, k+1 come with one 8-byte load per panel column
+        for (int k = p0 + 2 * tid; k < m; k += 2 * QT_THREADS) {
+            float2 v[QT_NB];
+#pragma unroll
+            for (int j = 0; j < QT_NB; ++j)
+                v[j] = j < pw ? *reinterpret_cast<const float2*>(A + (long)(p0 + j) * job.ld + k)
+                              : make_float2(0.f, 0.f);
             if (k < p0 + QT_NB) {  // the panel's triangle
 #pragma unroll
-                for (int j = 0; j < QT_NB; ++j)
-                    v[j] = j < pw ? qt_v(A, job.ld, p0, j, k, A[(long)(p0 + j) * job.ld + k]) : 0.f;
-            } else {
-#pragma unroll
-                for (int j = 0; j < QT_NB; ++j) v[j] = j < pw ? A[(long)(p0 + j) * job.ld + k] : 0.f;
+                for (int j = 0; j < QT_NB; ++j) {
+                    v[j].x = qt_v(A, job.ld, p0, j, k, v[j].x);
+                    v[j].y = qt_v(A, job.ld, p0, j, k + 1, v[j].y);
+                }
             }
 #pragma unroll 2
             for (int r = 0; r < QT_RB; ++r) {
                 const float4* zr = reinterpret_cast<const float4*>(Z2 + r * QT_NB);
-                float s = 0.f;
+                float s0 = 0.f, s1 = 0.f;
 #pragma unroll
                 for (int j4 = 0; j4 < QT_NB / 4; ++j4) {
                     const float4 z = zr[j4];
-                    s = fmaf(z.x, v[4 * j4], s);
-                    s = fmaf(z.y, v[4 * j4 + 1], s);
-                    s = fmaf(z.z, v[4 * j4 + 2], s);
-                    s = fmaf(z.w, v[4 * j4 + 3], s);
+                    s0 = fmaf(z.x, v[4 * j4].x, s0);
+                    s1 = fmaf(z.x, v[4 * j4].y, s1);
+                    s0 = fmaf(z.y, v[4 * j4 + 1].x, s0);
+                    s1 = fmaf(z.y, v[4 * j4 + 1].y, s1);
+                    s0 = fmaf(z.z, v[4 * j4 + 2].x, s0);
+                    s1 = fmaf(z.z, v[4 * j4 + 2].y, s1);
+                    s0 = fmaf(z.w, v[4 * j4 + 3].x, s0);
+                    s1 = fmaf(z.w, v[4 * j4 + 3].y, s1);
                 }
-                X[(size_t)r * ldx + k] -= s;
+                float2* xr = reinterpret_cast<float2*>(X + (size_t)r * ldx + k);
+                float2 x = *xr;
+                x.x -= s0;
+                x.y -= s1;
+                *xr = x;
             }
         }
         __syncthreads();
