@@ -135,10 +135,12 @@ def svd_flops(m, n):
 # Householder QR of every X_s^T (unit "qr"), the SVD sweep's factorisation of
 # every C_s for sigma and V ("svd", which the library runs as a pivoted QR of C
 # followed by one-sided Jacobi), and the contractions ("gemm").
+# qt_apply forms the product M Q^T from the stored reflectors (the float
+# paths' replacement of gemm_center): its algorithmic work is that product's.
 UNIT_OF = {"qr_lq_sweep": "qr", "qr_svd_precond": "svd", "jacobi_svd": "svd", "gemm_expand_absorb": "gemm",
-           "gemm_center": "gemm", "gemm_u": "gemm", "svd_finalize": "gemm"}
+           "gemm_center": "gemm", "qt_apply": "gemm", "gemm_u": "gemm", "svd_finalize": "gemm"}
 KERNELS_OF = {"qr": "k_qr (LQ sweep launches)", "svd": "k_qr (pivoted R-only launches) + k_jacobi_select",
-              "gemm": "k_gemm128 / k_gemm"}
+              "gemm": "k_gemm128 / k_gemm / k_gemm_tc / k_apply_qt"}
 
 
 def flop_models(w, D, n_applied=None):
@@ -149,7 +151,8 @@ def flop_models(w, D, n_applied=None):
     output bonds chi').  Per compression (one expanded term, Fig. 3):
       qr    sites L-1..1: Householder QR of X_s^T (m = 4 k_{s+1}, n = e_s), no Q formation
       svd   sites 0..L-2: sigma and V of C_s (m = 4 chi'_s, n = k_{s+1})
-      gemm  expand+absorb, M Q, U = C V^T, the projector correction: 2 M N K
+      gemm  expand+absorb, M Q (a GEMM, or the reflectors applied on the
+            float paths), U = C V^T, the projector correction: 2 M N K
     Returns ({unit: flops}, compressions).
     """
     L, N = w["L"], w["N"]
