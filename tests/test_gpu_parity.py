@@ -33,7 +33,7 @@ def B():
     return binding
 
 
-DT = {"fp64": torch.float64, "fp32": torch.float32}
+DT = {"fp64": torch.float64, "fp32": torch.float32, "tf32": torch.float32}
 
 
 def dev(a, dtype=torch.float64):
@@ -387,9 +387,11 @@ def block_L16(B):
 # order of rounding, not on the inputs: two builds that differ only in how two
 # square factors are preconditioned gave 1.9e-4 and 9.3e-4 (TF32: 5.3e-4 and
 # 3.1e-4), while rounding psi to float32 once moves the float64 path's
-# 96-term result by 1.0e-7.  2e-3 allowed.  This is far above the 1e-6 asked of
-# the mixed path, which dense float32 arithmetic does not reach at this size.
-@pytest.mark.parametrize("path,tolr", [("fp64", 1e-9), ("fp32", 2e-3)])
+# 96-term result by 1.0e-7.  2e-3 allowed, for the TF32 path (the bench's
+# path: same float32 storage, tensor-core contractions) as well.  This is far
+# above the 1e-6 asked of the mixed path, which dense float32 arithmetic does
+# not reach at this size.
+@pytest.mark.parametrize("path,tolr", [("fp64", 1e-9), ("fp32", 2e-3), ("tf32", 2e-3)])
 def test_apply_H_full_block_L16_N48_D128(B, block_L16, path, tolr):
     t, chi, zeta, psi, D, ref = block_L16
     out = B.thc_apply_H(dev(t), dev(chi), dev(zeta), [dev(a, DT[path]) for a in psi], D_max=D, path=path,
