@@ -58,3 +58,32 @@ def test_invalid_arguments_rejected_before_any_gpu_work(lib):
 def test_binding_names_match_header():
     from paper_2409_12708_gb300 import binding as B
     assert set(B.EXPORTED) == set(declared_functions())
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    # the binding's ctypes mirrors of the ABI structs against the C compiler's
+    # layout of include/thc.h (size and every field offset)
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    from paper_2409_12708_gb300 import binding as B
+    structs = {"thc_opts": B.thc_opts, "thc_mps": B.thc_mps, "thc_hamiltonian": B.thc_hamiltonian,
+               "thc_allocator": B.thc_allocator}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", f'#include "{HEADER}"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} sizeof %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call([cc, "-std=c11", str(src), "-o", str(exe)])
+    out = subprocess.check_output([str(exe)], text=True).split("\n")
+    c_layout = {(a, b): int(c) for a, b, c in (ln.split() for ln in out if ln.strip())}
+    for name, cls in structs.items():
+        assert c_layout[(name, "sizeof")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert c_layout[(name, field)] == getattr(cls, field).offset, (name, field)
