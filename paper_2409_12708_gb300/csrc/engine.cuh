@@ -30,6 +30,7 @@
 #include "qr.cuh"
 #include "qt_apply.cuh"
 #include "small.cuh"
+#include "terms.cuh"
 #include "tc_gemm.cuh"
 
 namespace thc {
@@ -476,46 +477,6 @@ __global__ void k_copy_batched(T* dst, long sdst, const T* src, long ssrc, long 
 //      source = reuse slot (s'*N + nu) - j_first;
 //    kinetic t -> (i, s): layer 1 = lambda_i sum_q u_qi a_{q s}, layer 2 = sum_p u_pi a+_{p s},
 //      source = 0 (psi itself).
-// Coulomb term list (Eq. G).  Unmerged: t = ((s'*N + nu)*2 + s)*N + mu, 4N^2
-// terms.  Spin-merged (symmetric zeta): the opposite-spin pair (mu down, nu up)
-// is folded into (mu up, nu down), which commute and carry the same zeta; the
-// list is block (nu, up) with mu up only (t < N^2), then block (nu, down)
-// with s = up (factor 2) and s = down, 3N^2 terms.  block = s'*N + nu is the
-// index of the reused state psi_{nu s'}.
-struct TermIdx {
-    int mu, s, nu, sp;
-    double factor;
-};
-__host__ __device__ inline long coulomb_terms(int N, int merge) { return (merge ? 3L : 4L) * N * N; }
-__host__ __device__ inline TermIdx decode_coulomb(long t, int N, int merge) {
-    TermIdx d;
-    d.factor = 1.0;
-    if (!merge) {
-        d.mu = (int)(t % N);
-        long rest = t / N;
-        d.s = (int)(rest % 2);
-        rest /= 2;
-        d.nu = (int)(rest % N);
-        d.sp = (int)(rest / N);
-    } else if (t < (long)N * N) {
-        d.mu = (int)(t % N);
-        d.s = 0;
-        d.nu = (int)(t / N);
-        d.sp = 0;
-    } else {
-        const long k = t - (long)N * N;
-        d.mu = (int)(k % N);
-        d.s = (int)((k / N) % 2);
-        d.nu = (int)(k / (2L * N));
-        d.sp = 1;
-        if (d.s == 0) d.factor = 2.0;
-    }
-    return d;
-}
-__host__ __device__ inline long coulomb_block(long t, int N, int merge) {
-    const TermIdx d = decode_coulomb(t, N, merge);
-    return (long)d.sp * N + d.nu;
-}
 
 template <class T>
 __global__ void k_term_coefs(int stage, long t0, int B, int L, int N, int merge, const double* chi,
