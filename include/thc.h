@@ -147,7 +147,8 @@ typedef struct {
  * the bond-2 ladder MPOs of the elementary-MPO equations is applied and
  * followed by the QR-then-SVD compression of Fig. 3, and the compressed terms
  * are summed by the pairwise reduction of Sec. 4.5.  psi must have dtype
- * F64 or C128 (path FP64), F32 or C64 (path FP32).  `out` receives a
+ * F64 or C128 (path FP64), F32 or C64 (paths FP32 and TF32; complex MPS run
+ * the TF32 path's contractions on the SIMT pipe).  `out` receives a
  * library-owned MPS of the same dtype whose bonds are at most D_max. */
 thc_status thc_apply_H(const thc_hamiltonian* H, const thc_mps* psi, const thc_opts* opts,
                        thc_mps* out, const thc_allocator* alloc, void* stream);
